@@ -1,0 +1,237 @@
+/*
+ * qk.h - C ABI of libqk: quantum-kernel Gram matrices from MPS simulation on
+ * one GB300 (sm_103a).
+ *
+ * The method (arXiv 2411.09336, Sec. II): every data vector x (m features ->
+ * m qubits) is encoded as |psi(x)> = U(x)|+>^m with
+ *   U(x) = (exp(-i H_XX) exp(-i H_Z))^r                               (Eq. 3)
+ *   H_Z  = gamma sum_k x_k Z_k                                          (Eq. 4)
+ *   H_XX = gamma^2 (pi/2) sum_{(i,j) in G} (1-x_i)(1-x_j) X_i X_j       (Eq. 5)
+ * G = all qubit pairs at distance 1..d on a line (Sec. II-C).  The state is
+ * simulated as a matrix product state, every two-qubit gate followed by an SVD
+ * truncation (Sec. II-B, Fig. 1, Eq. 8), and the kernel is
+ *   K_ij = |<psi(x_i)|psi(x_j)>|^2                                      (Eq. 1)
+ * contracted by the left-to-right transfer sweep of Fig. 2.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a qk_status.  On failure the outputs are left
+ *     untouched and qk_last_error() returns a message (thread-local).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; calls marked "synchronises" wait for
+ *     the stream before returning.
+ *   - Pointers marked "host or device" may point to either; the library looks
+ *     the pointer up (cudaPointerGetAttributes) and copies host data itself.
+ *   - Arguments are checked before any launch: a bad argument returns
+ *     QK_ERR_INVALID_ARG and launches nothing.
+ *   - Bounded device waits never trap: a wait that runs out sets an error word
+ *     that the host reads back as QK_ERR_TIMEOUT.
+ */
+#ifndef QK_H_
+#define QK_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QK_OK = 0,
+  QK_ERR_INVALID_ARG = 1,
+  QK_ERR_OOM = 2,
+  QK_ERR_CUDA = 3,
+  QK_ERR_NUMERIC = 4,  /* SVD sweep cap reached or a non-finite value */
+  QK_ERR_TIMEOUT = 5   /* a bounded device wait ran out */
+} qk_status;
+
+/* Overlap arithmetic. */
+typedef enum {
+  QK_PREC_FP64 = 0,       /* plain FP64 transfer sweep on the CUDA cores */
+  QK_PREC_SPLIT_BF16 = 1  /* tcgen05 tensor cores: operands split into bf16
+                             hi + lo, products hi*hi + hi*lo + lo*hi,
+                             FP32 accumulation */
+} qk_prec;
+
+/* Storage precision of the packed states (the build itself is FP64). */
+typedef enum { QK_STORE_C128 = 0, QK_STORE_C64 = 1 } qk_store;
+
+/* Opaque batch of N MPS states on one device, owned by the library. */
+typedef struct qk_mps_batch qk_mps_batch;
+/* Opaque surrogate network, owned by the library. */
+typedef struct qk_surrogate qk_surrogate;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* qk_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * qk_build_states - simulate |psi(x_s)> for s = 0..N-1 as MPS (Sec. II-B).
+ *
+ *   X        host or device, N x n float64, row-major (row s = x_s).  Used as
+ *            given: no rescaling is applied inside the method.
+ *   n        qubits = features, 2 <= n <= 1024.
+ *   d        interaction distance, 0 <= d <= n-1 (d = 0: product states).
+ *   reps     circuit repetitions r >= 1.
+ *   gamma    kernel bandwidth (finite).
+ *   chi_max  bond-dimension cap, 1 <= chi_max <= 128.
+ *   eps      truncation tolerance >= 0: after each two-site gate keep the
+ *            fewest singular values whose discarded squared tail is
+ *            <= eps^2 * (sum of all squares), then at most chi_max; the kept
+ *            values are rescaled to unit norm.  eps = 0: no truncation below
+ *            chi_max.  (Eq. 8: the discarded weight bounds the infidelity.)
+ *   store    storage precision of the result.
+ *   rank_trace  optional device int32 [N][reps * n_ops] (NULL to skip): the
+ *            rank kept after every two-site op, in execution order;
+ *            n_ops = qk_schedule_length(n, d).
+ *   out      receives the new batch (free with qk_mps_free).
+ * The build runs in FP64.  Two-site ops follow the SWAP-routed schedule:
+ * for each qubit i, Rxx(i,i+t) (t < k) fused with the following SWAP, then
+ * Rxx(i,i+k) and k-1 SWAPs back, k = min(d, n-1-i) (Sec. II-C).  Final
+ * states are left-canonical.  Synchronises.
+ * Errors: INVALID_ARG (ranges above, non-finite X or gamma), OOM, CUDA,
+ * NUMERIC (an SVD did not converge in its sweep cap).
+ * ---------------------------------------------------------------------- */
+qk_status qk_build_states(const double* X, int64_t N, int32_t n, int32_t d,
+                          int32_t reps, double gamma, int32_t chi_max,
+                          double eps, qk_store store, int32_t* rank_trace,
+                          void* stream, qk_mps_batch** out);
+
+/* Number of two-site ops in one repetition: sum_i (2 min(d, n-1-i) - 1). */
+int64_t qk_schedule_length(int32_t n, int32_t d);
+
+/* ------------------------------------------------------------------------
+ * qk_mps_import - wrap caller-supplied MPS as a batch (tests and tooling).
+ *   bond_dims  host int32 [N][n+1], chi_0 = chi_n = 1, each 1..chi_max_cap.
+ *   re_im      host float64, the sites of all states back to back: for state
+ *              s, site k, entry (a, q, b) of the tensor A_k[a][q][b]
+ *              (a < chi_k, q < 2, b < chi_{k+1}) stored as (re, im) at
+ *              2 * (off_s + off_k + (a*2 + q)*chi_{k+1} + b).
+ *   store      storage precision used for the batch.
+ * Synchronises.  Errors: INVALID_ARG, OOM, CUDA.
+ * ---------------------------------------------------------------------- */
+qk_status qk_mps_import(int64_t N, int32_t n, const int32_t* bond_dims,
+                        const double* re_im, qk_store store, void* stream,
+                        qk_mps_batch** out);
+
+/* Shape queries (host, no synchronisation). */
+qk_status qk_mps_shape(const qk_mps_batch* b, int64_t* N, int32_t* n);
+/* dims: host int32 [N][n+1].  Synchronises. */
+qk_status qk_mps_bond_dims(const qk_mps_batch* b, int32_t* dims);
+/* w: host float64 [N], summed discarded weight per state.  Synchronises. */
+qk_status qk_mps_trunc_weight(const qk_mps_batch* b, double* w);
+/* Stored bytes of the packed states (arena only). */
+qk_status qk_mps_bytes(const qk_mps_batch* b, int64_t* bytes);
+/* Copy state `s` to host in the qk_mps_import layout; `cap` is the length of
+ * re_im in doubles (>= 2 * sum_k chi_k * 2 * chi_{k+1}).  Synchronises. */
+qk_status qk_mps_export(const qk_mps_batch* b, int64_t s, double* re_im,
+                        int64_t cap);
+qk_status qk_mps_free(qk_mps_batch* b);
+
+/* ------------------------------------------------------------------------
+ * qk_gram - K[i][j] = |<psi(a_i)|psi(b_j)>|^2 for all i < N_A, j < N_B
+ * (Eq. 1) by the transfer sweep of Fig. 2.
+ *   A, B     batches with equal n.  B == A (same pointer) selects the
+ *            symmetric case: only i <= j is contracted and mirrored
+ *            (Sec. II-D: half of the entries).
+ *   K        host or device float64, row-major with leading dimension ldk
+ *            >= N_B; K[i*ldk + j].
+ *   prec     QK_PREC_FP64 or QK_PREC_SPLIT_BF16.
+ *   refine_floor  split path only: entries with K < refine_floor are
+ *            contracted again in FP64 (0 disables).
+ *   n_refined     optional host out: entries re-evaluated in FP64.
+ * Synchronises.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT.
+ * ---------------------------------------------------------------------- */
+qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, double* K,
+                  int64_t ldk, qk_prec prec, double refine_floor, void* stream,
+                  int64_t* n_refined);
+
+/* K_out[p] = |<psi(a_{pairs[2p]})|psi(b_{pairs[2p+1]})>|^2 for p < P.
+ * pairs: host or device int32 [P][2]; K_out: host or device float64 [P].
+ * Synchronises.  Errors: INVALID_ARG (index out of range), OOM, CUDA. */
+qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
+                        const int32_t* pairs, int64_t P, double* K_out,
+                        qk_prec prec, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate for log K (not in the paper).  A 3-layer MLP
+ *   f -> ReLU(W1 f + b1) -> ReLU(W2 h + b2) -> w3 . h + b3
+ * on the symmetric pair features f(x, y) = [(x - y)^2, (x + y)/2] (2n values),
+ * bf16 weights and activations in the products, FP32 accumulation and FP32
+ * master weights, Adam.  Its predictions of log K are accepted only where a
+ * split-conformal bound (per bin of predicted value) is within `tol`; every
+ * other entry falls back to the exact MPS overlap.
+ * ---------------------------------------------------------------------- */
+/* in_dim must be 2n, 16 <= in_dim <= 4096; hidden a multiple of 16 in
+ * [16, 1024].  Weights are He-uniform from a counter-based generator seeded
+ * by `seed`; biases zero. */
+qk_status qk_surrogate_create(int32_t in_dim, int32_t hidden, uint64_t seed,
+                              qk_surrogate** out);
+qk_status qk_surrogate_free(qk_surrogate* net);
+/* Parameter transfer in FP32, order W1[h][in], b1[h], W2[h][h], b2[h],
+ * W3[h], b3[1]; host buffers of qk_surrogate_param_count() floats. */
+int64_t qk_surrogate_param_count(const qk_surrogate* net);
+qk_status qk_surrogate_get_params(const qk_surrogate* net, float* params);
+qk_status qk_surrogate_set_params(qk_surrogate* net, const float* params);
+/* Target standardisation: the network fits (t - mean) / scale. */
+qk_status qk_surrogate_set_target_scale(qk_surrogate* net, double mean,
+                                        double scale);
+
+/* Loss and gradient of one batch, no update (for parity checks).
+ *   Xa, Xb   host or device float64 [Na][n], [Nb][n]; pairs [P][2] int32;
+ *   target   host or device float64 [P] (log K, before standardisation).
+ *   grads    optional host float32 [param_count], same order as params.
+ *   loss     optional host out: (1/2P) sum (yhat - t')^2 on standardised t'. */
+qk_status qk_surrogate_loss_grad(qk_surrogate* net, const double* Xa,
+                                 int64_t Na, const double* Xb, int64_t Nb,
+                                 int32_t n, const int32_t* pairs,
+                                 const double* target, int64_t P,
+                                 float* grads, double* loss, void* stream);
+/* Adam training: `epochs` passes over the P pairs in shuffled minibatches of
+ * `batch` (seeded by `seed`), learning rate lr, betas (0.9, 0.999), eps 1e-8.
+ * loss_out optional host float64: mean loss of the last epoch. */
+qk_status qk_surrogate_train(qk_surrogate* net, const double* Xa, int64_t Na,
+                             const double* Xb, int64_t Nb, int32_t n,
+                             const int32_t* pairs, const double* target,
+                             int64_t P, int32_t epochs, int32_t batch,
+                             float lr, uint64_t seed, void* stream,
+                             double* loss_out);
+/* Predicted log K (de-standardised) for P pairs; y: host or device float64. */
+qk_status qk_surrogate_predict(const qk_surrogate* net, const double* Xa,
+                               int64_t Na, const double* Xb, int64_t Nb,
+                               int32_t n, const int32_t* pairs, int64_t P,
+                               double* y, void* stream);
+/* Split-conformal calibration on held-out exact log K: n_bins equal-count
+ * bins of predicted value, per-bin bound = ceil((m+1)(1-alpha))-th smallest
+ * |pred - truth| (inf where a bin is too small).  Synchronises. */
+qk_status qk_surrogate_calibrate(qk_surrogate* net, const double* Xa,
+                                 int64_t Na, const double* Xb, int64_t Nb,
+                                 int32_t n, const int32_t* pairs,
+                                 const double* truth, int64_t P, double alpha,
+                                 int32_t n_bins, void* stream);
+/* Per-bin bounds after calibration: edges host [n_bins+1], bounds [n_bins]. */
+qk_status qk_surrogate_bins(const qk_surrogate* net, int32_t* n_bins,
+                            double* edges, double* bounds);
+
+/* ------------------------------------------------------------------------
+ * qk_gram_surrogate - the N_A x N_B block K[i][j] (test-vs-train use) with
+ * the surrogate first: where the calibrated bound of the predicted log K is
+ * <= tol the entry is exp(prediction), otherwise it is the exact overlap of
+ * states A[i], B[j] computed with `prec`.
+ *   Xa, Xb    the data vectors of A and B (host or device, float64 [N][n]).
+ *   K         host or device float64, leading dimension ldk.
+ *   accepted  optional host or device uint8 [N_A][N_B]: 1 where the surrogate
+ *             value was used.
+ *   n_accepted optional host out.
+ * Synchronises.  Errors: INVALID_ARG (uncalibrated net, shape mismatch), OOM,
+ * CUDA.
+ * ---------------------------------------------------------------------- */
+qk_status qk_gram_surrogate(const qk_surrogate* net, const qk_mps_batch* A,
+                            const qk_mps_batch* B, const double* Xa,
+                            const double* Xb, double tol, double* K,
+                            int64_t ldk, uint8_t* accepted, qk_prec prec,
+                            void* stream, int64_t* n_accepted);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QK_H_ */

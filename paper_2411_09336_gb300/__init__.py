@@ -1,0 +1,221 @@
+"""Python binding of libqk (quantum-kernel Gram matrices via MPS on GB300).
+
+Argument marshalling only: every step of the computation runs in libqk's CUDA
+kernels.  Functions carry the C names of include/qk.h.  PyTorch provides device
+memory and streams; arrays may be numpy arrays (host) or torch tensors (host
+or CUDA), passed to the library as raw pointers.
+
+The library must have been built (python -c "import __graft_entry__ as g;
+g.build()" or python paper_2411_09336_gb300/build.py); importing this package
+without libqk.so raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqk.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libqk.so is not built ({LIB_PATH}); run paper_2411_09336_gb300/build.py")
+
+_lib = C.CDLL(LIB_PATH)
+
+QK_OK, QK_ERR_INVALID_ARG, QK_ERR_OOM, QK_ERR_CUDA, QK_ERR_NUMERIC, QK_ERR_TIMEOUT = range(6)
+QK_PREC_FP64, QK_PREC_SPLIT_BF16 = 0, 1
+QK_STORE_C128, QK_STORE_C64 = 0, 1
+_PREC = {"fp64": QK_PREC_FP64, "split": QK_PREC_SPLIT_BF16, "split_bf16": QK_PREC_SPLIT_BF16}
+_STORE = {"c128": QK_STORE_C128, "c64": QK_STORE_C64}
+
+_vp, _i32, _i64, _f64, _f32, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float, C.c_uint64
+
+
+def _sig(name, args, res=C.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("qk_last_error", [], C.c_char_p)
+_sig("qk_schedule_length", [_i32, _i32], _i64)
+_sig("qk_build_states", [_vp, _i64, _i32, _i32, _i32, _f64, _i32, _f64, C.c_int, _vp, _vp, C.POINTER(_vp)])
+_sig("qk_mps_import", [_i64, _i32, _vp, _vp, C.c_int, _vp, C.POINTER(_vp)])
+_sig("qk_mps_shape", [_vp, C.POINTER(_i64), C.POINTER(_i32)])
+_sig("qk_mps_bond_dims", [_vp, _vp])
+_sig("qk_mps_trunc_weight", [_vp, _vp])
+_sig("qk_mps_bytes", [_vp, C.POINTER(_i64)])
+_sig("qk_mps_export", [_vp, _i64, _vp, _i64])
+_sig("qk_mps_free", [_vp])
+_sig("qk_gram", [_vp, _vp, _vp, _i64, C.c_int, _f64, _vp, C.POINTER(_i64)])
+_sig("qk_gram_pairs", [_vp, _vp, _vp, _i64, _vp, C.c_int, _vp])
+
+
+class QKError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.qk_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != QK_OK:
+        raise QKError(st, where)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (which must stay alive)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    ptr = getattr(a, "data_ptr", None)
+    if ptr is not None:
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as_f64(X):
+    if isinstance(X, np.ndarray):
+        return np.ascontiguousarray(X, dtype=np.float64)
+    import torch
+    return X.to(torch.float64).contiguous()
+
+
+def qk_schedule_length(n: int, d: int) -> int:
+    return int(_lib.qk_schedule_length(n, d))
+
+
+class MPSBatch:
+    """Handle of a library-owned batch of MPS states (qk_mps_batch*)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+        N = _i64()
+        n = _i32()
+        _check(_lib.qk_mps_shape(self._h, C.byref(N), C.byref(n)), "qk_mps_shape")
+        self.N, self.n = N.value, n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bond_dims(self) -> np.ndarray:
+        out = np.zeros((self.N, self.n + 1), dtype=np.int32)
+        _check(_lib.qk_mps_bond_dims(self._h, out.ctypes.data), "qk_mps_bond_dims")
+        return out
+
+    def trunc_weight(self) -> np.ndarray:
+        out = np.zeros(self.N, dtype=np.float64)
+        _check(_lib.qk_mps_trunc_weight(self._h, out.ctypes.data), "qk_mps_trunc_weight")
+        return out
+
+    def nbytes(self) -> int:
+        b = _i64()
+        _check(_lib.qk_mps_bytes(self._h, C.byref(b)), "qk_mps_bytes")
+        return b.value
+
+    def export(self, s: int) -> list:
+        """State s as a list of site tensors A_k[a, q, b] (complex128)."""
+        dims = self.bond_dims()[s]
+        cap = int(sum(4 * dims[k] * dims[k + 1] for k in range(self.n)))
+        buf = np.zeros(cap, dtype=np.float64)
+        _check(_lib.qk_mps_export(self._h, s, buf.ctypes.data, cap), "qk_mps_export")
+        z = buf[0::2] + 1j * buf[1::2]
+        out, o = [], 0
+        for k in range(self.n):
+            cnt = 2 * dims[k] * dims[k + 1]
+            out.append(z[o:o + cnt].reshape(dims[k], 2, dims[k + 1]))
+            o += cnt
+        return out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.qk_mps_free(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def qk_build_states(X, d: int, reps: int, gamma: float, chi_max: int, eps: float,
+                    store: str = "c64", rank_trace=None, stream=None) -> MPSBatch:
+    """Simulate every row of X (N x n, host or device) as an MPS (qk.h)."""
+    X = _as_f64(X)
+    N, n = X.shape
+    h = _vp()
+    _check(_lib.qk_build_states(_ptr(X), N, n, d, reps, float(gamma), chi_max, float(eps),
+                                _STORE[store], _ptr(rank_trace), _stream_ptr(stream), C.byref(h)),
+           "qk_build_states")
+    return MPSBatch(h.value)
+
+
+def qk_mps_import(states: list, store: str = "c64", stream=None) -> MPSBatch:
+    """Wrap a list of MPS (each a list of (chi_k, 2, chi_k+1) arrays) as a batch."""
+    N = len(states)
+    n = len(states[0])
+    dims = np.zeros((N, n + 1), dtype=np.int32)
+    flat = []
+    for s, st in enumerate(states):
+        dims[s, 0] = 1
+        for k, A in enumerate(st):
+            dims[s, k + 1] = A.shape[2]
+            z = np.ascontiguousarray(A, dtype=np.complex128).reshape(-1)
+            flat.append(np.stack([z.real, z.imag], axis=1).reshape(-1))
+    buf = np.ascontiguousarray(np.concatenate(flat))
+    h = _vp()
+    _check(_lib.qk_mps_import(N, n, dims.ctypes.data, buf.ctypes.data, _STORE[store],
+                              _stream_ptr(stream), C.byref(h)), "qk_mps_import")
+    return MPSBatch(h.value)
+
+
+def qk_gram(A: MPSBatch, B: MPSBatch | None = None, prec: str = "fp64", refine_floor: float = 0.0,
+            out=None, stream=None):
+    """Gram block K[i, j] = |<a_i|b_j>|^2 (B None or B is A: symmetric).
+
+    Returns (K, n_refined); K is `out` if given (numpy or torch, host or
+    device, float64, shape (N_A, N_B)), else a new CUDA torch tensor."""
+    import torch
+    sym = B is None or B is A
+    B = A if sym else B
+    if out is None:
+        out = torch.empty((A.N, B.N), dtype=torch.float64, device="cuda")
+    nref = _i64()
+    _check(_lib.qk_gram(A.handle, B.handle, _ptr(out), B.N, _PREC[prec], float(refine_floor),
+                        _stream_ptr(stream), C.byref(nref)), "qk_gram")
+    return out, nref.value
+
+
+def qk_gram_pairs(A: MPSBatch, B: MPSBatch, pairs, prec: str = "fp64", out=None, stream=None):
+    """K[p] = |<a_{pairs[p,0]}|b_{pairs[p,1]}>|^2; pairs int32 (P, 2)."""
+    import torch
+    if isinstance(pairs, np.ndarray):
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+    P = pairs.shape[0]
+    if out is None:
+        out = torch.empty(P, dtype=torch.float64, device="cuda")
+    _check(_lib.qk_gram_pairs(A.handle, B.handle, _ptr(pairs), P, _ptr(out), _PREC[prec],
+                              _stream_ptr(stream)), "qk_gram_pairs")
+    return out

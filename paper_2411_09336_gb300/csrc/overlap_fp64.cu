@@ -1,0 +1,195 @@
+// Plain FP64 transfer sweep (Fig. 2) on the CUDA cores: one CTA per pair,
+// persistent over a pair list.  Per site k the environment E (chi^a_k x
+// chi^b_k, FP64 complex) absorbs the site pair in the cheaper of the two
+// orders:
+//   (a) T_s = E B_k[s],            E' = sum_s A_k[s]^H T_s
+//   (b) F_s = A_k[s]^H E,          E' = sum_s F_s B_k[s]
+// E and the intermediates live in a per-CTA scratch slice (L1/L2 resident).
+// The storage precision of the states (complex64 or complex128) is read and
+// widened to FP64; every product and sum is FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qk_internal.h"
+
+namespace qk {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename C>
+__device__ __forceinline__ double2 ld(const C* p, int64_t i);
+template <>
+__device__ __forceinline__ double2 ld<double2>(const double2* p, int64_t i) {
+  return p[i];
+}
+template <>
+__device__ __forceinline__ double2 ld<float2>(const float2* p, int64_t i) {
+  float2 v = p[i];
+  return make_double2((double)v.x, (double)v.y);
+}
+
+struct PairArgs {
+  const uint64_t* a_ptr;   // [NA][n] site addresses of A
+  const int32_t* a_dims;   // [NA][n+1]
+  const uint64_t* b_ptr;
+  const int32_t* b_dims;
+  int n;
+  const int32_t* pairs;    // [P][2]
+  int64_t P;
+  double* K;               // output
+  int64_t ldk;             // >0: K[i*ldk + j] (and mirror if sym); 0: K[p]
+  int sym;
+  double2* scratch;        // per CTA 3 * cap
+  int64_t cap;
+  int* queue;
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kThreads) overlap_fp64_kernel(PairArgs a) {
+  __shared__ int s_pair;
+  double2* E = a.scratch + (int64_t)blockIdx.x * 3 * a.cap;
+  double2* T = E + a.cap;
+  double2* E2 = T + a.cap;
+  const int n = a.n;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_pair = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int64_t pi = s_pair;
+    if (pi >= a.P) break;
+    const int i = a.pairs[2 * pi], j = a.pairs[2 * pi + 1];
+    const uint64_t* pa = a.a_ptr + (int64_t)i * n;
+    const uint64_t* pb = a.b_ptr + (int64_t)j * n;
+    const int32_t* da = a.a_dims + (int64_t)i * (n + 1);
+    const int32_t* db = a.b_dims + (int64_t)j * (n + 1);
+    if (threadIdx.x == 0) E[0] = make_double2(1.0, 0.0);
+    __syncthreads();
+    double2* Ecur = E;
+    double2* Enext = E2;
+    for (int k = 0; k < n; ++k) {
+      const int xa = da[k], ua = da[k + 1], xb = db[k], yb = db[k + 1];
+      const C* A = reinterpret_cast<const C*>(pa[k]);
+      const C* B = reinterpret_cast<const C*>(pb[k]);
+      const double costA = (double)xa * xb * yb + (double)ua * xa * yb;
+      const double costB = (double)ua * xa * xb + (double)ua * xb * yb;
+      if (costA <= costB) {
+        // T[s][x][y] = sum_c E[x][c] B[s][c][y]
+        for (int o = threadIdx.x; o < 2 * xa * yb; o += kThreads) {
+          int s = o / (xa * yb), rem = o % (xa * yb), x = rem / yb, y = rem % yb;
+          const double2* er = Ecur + (int64_t)x * xb;
+          const C* bc = B + (int64_t)s * xb * yb + y;
+          double re = 0.0, im = 0.0;
+          for (int c = 0; c < xb; ++c) {
+            double2 e = er[c], b = ld(bc, (int64_t)c * yb);
+            re = fma(e.x, b.x, fma(-e.y, b.y, re));
+            im = fma(e.x, b.y, fma(e.y, b.x, im));
+          }
+          T[o] = make_double2(re, im);
+        }
+        __syncthreads();
+        // E'[u][y] = sum_s sum_x conj(A[s][x][u]) T[s][x][y]
+        for (int o = threadIdx.x; o < ua * yb; o += kThreads) {
+          int u = o / yb, y = o % yb;
+          double re = 0.0, im = 0.0;
+          for (int s = 0; s < 2; ++s)
+            for (int x = 0; x < xa; ++x) {
+              double2 av = ld(A, ((int64_t)s * xa + x) * ua + u);
+              double2 t = T[((int64_t)s * xa + x) * yb + y];
+              re = fma(av.x, t.x, fma(av.y, t.y, re));
+              im = fma(av.x, t.y, fma(-av.y, t.x, im));
+            }
+          Enext[o] = make_double2(re, im);
+        }
+      } else {
+        // F[s][u][c] = sum_x conj(A[s][x][u]) E[x][c]
+        for (int o = threadIdx.x; o < 2 * ua * xb; o += kThreads) {
+          int s = o / (ua * xb), rem = o % (ua * xb), u = rem / xb, c = rem % xb;
+          double re = 0.0, im = 0.0;
+          for (int x = 0; x < xa; ++x) {
+            double2 av = ld(A, ((int64_t)s * xa + x) * ua + u);
+            double2 e = Ecur[(int64_t)x * xb + c];
+            re = fma(av.x, e.x, fma(av.y, e.y, re));
+            im = fma(av.x, e.y, fma(-av.y, e.x, im));
+          }
+          T[o] = make_double2(re, im);
+        }
+        __syncthreads();
+        // E'[u][y] = sum_s sum_c F[s][u][c] B[s][c][y]
+        for (int o = threadIdx.x; o < ua * yb; o += kThreads) {
+          int u = o / yb, y = o % yb;
+          double re = 0.0, im = 0.0;
+          for (int s = 0; s < 2; ++s)
+            for (int c = 0; c < xb; ++c) {
+              double2 f = T[((int64_t)s * ua + u) * xb + c];
+              double2 b = ld(B, ((int64_t)s * xb + c) * yb + y);
+              re = fma(f.x, b.x, fma(-f.y, b.y, re));
+              im = fma(f.x, b.y, fma(f.y, b.x, im));
+            }
+          Enext[o] = make_double2(re, im);
+        }
+      }
+      __syncthreads();
+      double2* tmp = Ecur;
+      Ecur = Enext;
+      Enext = tmp;
+    }
+    if (threadIdx.x == 0) {
+      double2 z = Ecur[0];
+      double kv = z.x * z.x + z.y * z.y;
+      if (a.ldk > 0) {
+        a.K[(int64_t)i * a.ldk + j] = kv;
+        if (a.sym) a.K[(int64_t)j * a.ldk + i] = kv;
+      } else {
+        a.K[pi] = kv;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// Contract the listed pairs in FP64.  ldk > 0 writes K[i*ldk + j] (mirrored
+// when sym), ldk == 0 writes K[p].
+qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
+                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st) {
+  if (P == 0) return QK_OK;
+  int dev = 0, sms = 0;
+  QK_CUDA(cudaGetDevice(&dev));
+  QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int chi = std::max(A->chi_cap, B->chi_cap);
+  int64_t cap = 2LL * chi * chi;
+  int64_t ctas = std::min<int64_t>((int64_t)sms * 4, P);
+  double2* scratch = nullptr;
+  int* queue = nullptr;
+  QK_CUDA(cudaMallocAsync(&scratch, sizeof(double2) * 3 * cap * ctas, st));
+  QK_CUDA(cudaMallocAsync(&queue, sizeof(int), st));
+  QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), st));
+  PairArgs a;
+  a.a_ptr = A->d_site_ptr;
+  a.a_dims = A->d_dims;
+  a.b_ptr = B->d_site_ptr;
+  a.b_dims = B->d_dims;
+  a.n = A->n;
+  a.pairs = d_pairs;
+  a.P = P;
+  a.K = dK;
+  a.ldk = ldk;
+  a.sym = sym ? 1 : 0;
+  a.scratch = scratch;
+  a.cap = cap;
+  a.queue = queue;
+  if (A->store == QK_STORE_C64)
+    overlap_fp64_kernel<float2><<<(int)ctas, kThreads, 0, st>>>(a);
+  else
+    overlap_fp64_kernel<double2><<<(int)ctas, kThreads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(scratch, st);
+  cudaFreeAsync(queue, st);
+  if (e != cudaSuccess) return cuda_fail(e, "overlap_fp64_kernel launch");
+  return QK_OK;
+}
+
+}  // namespace qk

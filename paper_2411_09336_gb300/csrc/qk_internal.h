@@ -1,0 +1,76 @@
+// Internal declarations shared by the libqk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qk.h"
+
+namespace qk {
+
+// ---- error state (thread-local message, see qk_last_error) ----------------
+void set_error(const std::string& msg);
+qk_status fail(qk_status st, const std::string& msg);
+qk_status cuda_fail(cudaError_t e, const char* what);
+
+#define QK_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::qk::cuda_fail(e_, #call); \
+  } while (0)
+
+// ---- two-site op schedule (Sec. II-C) -------------------------------------
+enum OpKind : int32_t { OP_RXX = 0, OP_SWAP_RXX = 1, OP_SWAP = 2 };
+struct Op {
+  int32_t kind;  // OpKind
+  int32_t p;     // acts on positions (p, p+1)
+  int32_t qi;    // Rxx qubits (qi, qj); -1 for a bare SWAP
+  int32_t qj;
+};
+std::vector<Op> make_schedule(int n, int d);
+
+// ---- device memory helpers --------------------------------------------------
+// Copies `bytes` from a host-or-device pointer into a fresh device buffer when
+// the source is host memory; returns the device pointer to use.  `owned`
+// receives the buffer to free (nullptr when src is already device memory).
+qk_status to_device(const void* src, size_t bytes, cudaStream_t st,
+                    const void** dev, void** owned);
+bool is_device_ptr(const void* p);
+
+// ---- MPS batch -------------------------------------------------------------
+// Site k of state s is the tensor A[q][a][b] (q < 2, a < chi_k,
+// b < chi_{k+1}), row-major, complex (re, im) interleaved, in the storage
+// precision; site_ptr[s*n + k] is its device address.
+struct Chunk {
+  void* ptr;
+  size_t bytes;
+};
+
+}  // namespace qk
+
+struct qk_mps_batch {
+  int device = 0;
+  int64_t N = 0;
+  int32_t n = 0;
+  qk_store store = QK_STORE_C64;
+  int32_t chi_cap = 1;  // largest bond dimension present
+  std::vector<qk::Chunk> chunks;     // arena allocations
+  int32_t* d_dims = nullptr;         // [N][n+1]
+  uint64_t* d_site_ptr = nullptr;    // [N][n]
+  double* d_trunc_w = nullptr;       // [N]
+  std::vector<int32_t> h_dims;       // host copy [N][n+1]
+  std::vector<uint64_t> h_site_ptr;  // host copy [N][n]
+  std::vector<double> h_trunc_w;
+  int64_t arena_bytes = 0;
+  // tensor-core operand cache (built on first split-precision use)
+  void* tc_cache = nullptr;
+};
+
+namespace qk {
+size_t elem_bytes(qk_store s);
+void free_batch_memory(qk_mps_batch* b);
+void free_tc_cache(qk_mps_batch* b);
+}  // namespace qk
