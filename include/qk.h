@@ -46,11 +46,20 @@ typedef enum {
 
 /* Overlap arithmetic. */
 typedef enum {
-  QK_PREC_FP64 = 0,       /* plain FP64 transfer sweep on the CUDA cores */
-  QK_PREC_SPLIT_BF16 = 1  /* tcgen05 tensor cores: operands split into bf16
-                             hi + lo, products hi*hi + hi*lo + lo*hi,
-                             FP32 accumulation */
+  QK_PREC_FP64 = 0,         /* plain FP64 transfer sweep on the CUDA cores */
+  QK_PREC_SPLIT_BF16 = 1,   /* tcgen05 tensor cores: operands split into bf16
+                               hi + lo (residual <= 2^-17), products
+                               hi*hi + hi*lo + lo*hi, FP32 accumulation */
+  QK_PREC_SPLIT_BF16X3 = 2  /* as above with three bf16 parts (exact for
+                               FP32 values) and the six products of order
+                               >= 2^-16: FP32-level accuracy, twice the MMAs */
 } qk_prec;
+
+/* The split path's error is relative to |<a|b>| (FP32 accumulation in the
+ * tensor cores truncates, a bias that grows with n), so entries with
+ * K > QK_SPLIT_REFINE_ABOVE are always re-evaluated in FP64; this keeps
+ * |dK| <= 1e-5 absolute for n up to a few hundred qubits. */
+#define QK_SPLIT_REFINE_ABOVE 1e-3
 
 /* Storage precision of the packed states (the build itself is FP64). */
 typedef enum { QK_STORE_C128 = 0, QK_STORE_C64 = 1 } qk_store;
@@ -134,9 +143,10 @@ qk_status qk_mps_free(qk_mps_batch* b);
  *            (Sec. II-D: half of the entries).
  *   K        host or device float64, row-major with leading dimension ldk
  *            >= N_B; K[i*ldk + j].
- *   prec     QK_PREC_FP64 or QK_PREC_SPLIT_BF16.
+ *   prec     QK_PREC_FP64, QK_PREC_SPLIT_BF16 or QK_PREC_SPLIT_BF16X3.
  *   refine_floor  split path only: entries with K < refine_floor are
- *            contracted again in FP64 (0 disables).
+ *            contracted again in FP64 (0 disables); entries with
+ *            K > QK_SPLIT_REFINE_ABOVE always are.
  *   n_refined     optional host out: entries re-evaluated in FP64.
  * Synchronises.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT.
  * ---------------------------------------------------------------------- */
@@ -145,6 +155,7 @@ qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, double* K,
                   int64_t* n_refined);
 
 /* K_out[p] = |<psi(a_{pairs[2p]})|psi(b_{pairs[2p+1]})>|^2 for p < P.
+ * The split path re-evaluates entries above QK_SPLIT_REFINE_ABOVE in FP64.
  * pairs: host or device int32 [P][2]; K_out: host or device float64 [P].
  * Synchronises.  Errors: INVALID_ARG (index out of range), OOM, CUDA. */
 qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,

@@ -25,9 +25,11 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 QK_OK, QK_ERR_INVALID_ARG, QK_ERR_OOM, QK_ERR_CUDA, QK_ERR_NUMERIC, QK_ERR_TIMEOUT = range(6)
-QK_PREC_FP64, QK_PREC_SPLIT_BF16 = 0, 1
+QK_PREC_FP64, QK_PREC_SPLIT_BF16, QK_PREC_SPLIT_BF16X3 = 0, 1, 2
 QK_STORE_C128, QK_STORE_C64 = 0, 1
-_PREC = {"fp64": QK_PREC_FP64, "split": QK_PREC_SPLIT_BF16, "split_bf16": QK_PREC_SPLIT_BF16}
+QK_SPLIT_REFINE_ABOVE = 1e-3  # mirrors include/qk.h
+_PREC = {"fp64": QK_PREC_FP64, "split": QK_PREC_SPLIT_BF16, "split_bf16": QK_PREC_SPLIT_BF16,
+         "split_bf16x3": QK_PREC_SPLIT_BF16X3}
 _STORE = {"c128": QK_STORE_C128, "c64": QK_STORE_C64}
 
 _vp, _i32, _i64, _f64, _f32, _u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float, C.c_uint64

@@ -73,10 +73,14 @@ qk_status build_states_device(const double* dX, int64_t N, int n, int d, int rep
                               cudaStream_t st, qk_mps_batch* out);
 qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
                        int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st);
-qk_status gram_split(const qk_mps_batch* A, const qk_mps_batch* B, double* dK, int64_t ldk,
-                     double refine_floor, cudaStream_t st, int64_t* n_refined);
-qk_status pairs_split(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
-                      int64_t P, double* dK, cudaStream_t st);
+qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK,
+                     int64_t ldk, double refine_floor, cudaStream_t st, int64_t* n_refined);
+qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B,
+                      const int32_t* d_pairs, int64_t P, double* dK, cudaStream_t st);
+static bool valid_prec(qk_prec p) {
+  return p == QK_PREC_FP64 || p == QK_PREC_SPLIT_BF16 || p == QK_PREC_SPLIT_BF16X3;
+}
+static int split_parts(qk_prec p) { return p == QK_PREC_SPLIT_BF16X3 ? 3 : 2; }
 
 // Host copies of the tables + derived sizes after the device tables are set.
 static qk_status finish_batch(qk_mps_batch* b, cudaStream_t st) {
@@ -339,7 +343,7 @@ extern "C" qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, doubl
   if (rc != QK_OK) return rc;
   if (!K) return fail(QK_ERR_INVALID_ARG, "qk_gram: K is NULL");
   if (ldk < B->N) return fail(QK_ERR_INVALID_ARG, "qk_gram: ldk < N_B");
-  if (prec != QK_PREC_FP64 && prec != QK_PREC_SPLIT_BF16) return fail(QK_ERR_INVALID_ARG, "qk_gram: bad precision");
+  if (!valid_prec(prec)) return fail(QK_ERR_INVALID_ARG, "qk_gram: bad precision");
   if (!(refine_floor >= 0.0)) return fail(QK_ERR_INVALID_ARG, "qk_gram: refine_floor must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   const bool sym = (A == B);
@@ -369,7 +373,7 @@ extern "C" qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, doubl
     rc = overlap_fp64(A, B, dp, P, dK, ldk, sym, st);
     cudaFreeAsync(dp, st);
   } else {
-    rc = gram_split(A, B, dK, ldk, refine_floor, st, n_refined);
+    rc = gram_split(split_parts(prec), A, B, dK, ldk, refine_floor, st, n_refined);
   }
   if (rc == QK_OK && host_k) {
     cudaError_t e = cudaMemcpyAsync(K, dK, kb, cudaMemcpyDeviceToHost, st);
@@ -388,7 +392,7 @@ extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
   if (P < 0 || P >= ((int64_t)1 << 31)) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: P out of range");
   if (P == 0) return QK_OK;
   if (!pairs || !K_out) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: NULL argument");
-  if (prec != QK_PREC_FP64 && prec != QK_PREC_SPLIT_BF16) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: bad precision");
+  if (!valid_prec(prec)) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: bad precision");
   cudaStream_t st = (cudaStream_t)stream;
   // validate the indices on the host
   std::vector<int32_t> hp;
@@ -416,7 +420,7 @@ extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
   if (prec == QK_PREC_FP64)
     rc = overlap_fp64(A, B, (const int32_t*)dp, P, dK, 0, false, st);
   else
-    rc = pairs_split(A, B, (const int32_t*)dp, P, dK, st);
+    rc = pairs_split(split_parts(prec), A, B, (const int32_t*)dp, P, dK, st);
   if (rc == QK_OK && host_k) {
     cudaError_t e = cudaMemcpyAsync(K_out, dK, sizeof(double) * P, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(K D2H)");

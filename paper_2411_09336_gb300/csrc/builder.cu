@@ -92,6 +92,9 @@ struct Shared {
   int perm[kMaxCols];    // sorted position -> column
   double tail[kMaxCols + 1];
   int chi[kMaxN + 1];
+  double pa[kMaxCols / 2], pb[kMaxCols / 2], pgr[kMaxCols / 2], pgi[kMaxCols / 2];
+  double pc[kMaxCols / 2], psx[kMaxCols / 2], psy[kMaxCols / 2];
+  int pidx[kMaxCols / 2];
   int rotated;
   int r;
   int sample;
@@ -101,65 +104,112 @@ struct Shared {
 };
 
 // One-sided Jacobi on the `cols` columns (length `rows`, column-major) of W.
-// Returns false if the sweep cap was reached.
+// A round of the round-robin ordering rotates up to cols/2 disjoint pairs in
+// three phases: (A) a team of T lanes forms |c_p|^2, |c_q|^2 and c_p^H c_q
+// for each pair, (B) one thread per pair turns them into the rotation (so the
+// FP64 divisions and square roots are done once per pair, not once per lane),
+// (C) the team applies it.  Returns false if the sweep cap was reached.
 __device__ bool jacobi(double2* W, int rows, int cols, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int npad = cols + (cols & 1);
+  const int npairs = npad / 2;
   const double tol = (double)(rows > 32 ? rows : 32) * 2.220446049250313e-16;
   if (cols < 2) return true;
+  // team size: about 8 rows per lane, 4..32 lanes
+  int T = 4;
+  while (T < 32 && T * 8 < rows) T <<= 1;
+  const int per_warp = 32 / T;
+  const int team = warp * per_warp + lane / T;
+  const int tl = lane % T;
+  const int nteams = kWarps * per_warp;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (threadIdx.x == 0) sh.rotated = 0;
     __syncthreads();
     for (int round = 0; round < npad - 1; ++round) {
-      for (int k = warp; k < npad / 2; k += kWarps) {
-        int p, q;
-        if (k == 0) {
-          p = npad - 1;
-          q = round;
-        } else {
-          p = (round + k) % (npad - 1);
-          q = (round - k + (npad - 1)) % (npad - 1);
+      // (A) inner products; the loop is uniform across the warp so every
+      // lane reaches the team shuffles
+      for (int kb = warp * per_warp; kb < npairs; kb += nteams) {
+        const int k = kb + lane / T;
+        int p = npad, q = npad;
+        if (k < npairs) {
+          if (k == 0) {
+            p = npad - 1;
+            q = round;
+          } else {
+            p = (round + k) % (npad - 1);
+            q = (round - k + (npad - 1)) % (npad - 1);
+          }
         }
-        if (p >= cols || q >= cols) continue;
+        const bool valid = p < cols && q < cols;
+        double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
+        if (valid) {
+          const double2* cp = W + (int64_t)p * rows;
+          const double2* cq = W + (int64_t)q * rows;
+          for (int i = tl; i < rows; i += T) {
+            double2 u = cp[i], v = cq[i];
+            a = fma(u.x, u.x, fma(u.y, u.y, a));
+            b = fma(v.x, v.x, fma(v.y, v.y, b));
+            gr = fma(u.x, v.x, fma(u.y, v.y, gr));   // Re(conj(u) v)
+            gi = fma(u.x, v.y, fma(-u.y, v.x, gi));  // Im(conj(u) v)
+          }
+        }
+        for (int o = T >> 1; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          gr += __shfl_xor_sync(0xffffffffu, gr, o);
+          gi += __shfl_xor_sync(0xffffffffu, gi, o);
+        }
+        if (tl == 0 && k < npairs) {
+          sh.pa[k] = a;
+          sh.pb[k] = b;
+          sh.pgr[k] = gr;
+          sh.pgi[k] = gi;
+          sh.pidx[k] = valid ? (p | (q << 16)) : -1;
+        }
+      }
+      __syncthreads();
+      // (B) rotation parameters, one thread per pair
+      for (int k = threadIdx.x; k < npairs; k += kThreads) {
+        double a = sh.pa[k], b = sh.pb[k], gr = sh.pgr[k], gi = sh.pgi[k];
+        double g = sqrt(gr * gr + gi * gi);
+        bool rot = sh.pidx[k] >= 0 && a != 0.0 && b != 0.0 && g > tol * sqrt(a) * sqrt(b);
+        double c = 1.0, sx = 0.0, sy = 0.0;
+        if (rot) {
+          // [[c, s e^{i phi}], [-s e^{-i phi}, c]] zeroes conj(c_p) c_q
+          double zeta = (b - a) / (2.0 * g);
+          double t = fabs(zeta) > 1e100
+                         ? 0.5 / zeta
+                         : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          if (t == 0.0) {
+            rot = false;
+          } else {
+            c = 1.0 / sqrt(1.0 + t * t);
+            double s = c * t;
+            sx = s * gr / g;  // s e^{i phi} = (sx, sy)
+            sy = s * gi / g;
+          }
+        }
+        sh.pc[k] = rot ? c : 0.0;  // 0 marks "no rotation"
+        sh.psx[k] = sx;
+        sh.psy[k] = sy;
+        if (rot) atomicAdd(&sh.rotated, 1);
+      }
+      __syncthreads();
+      // (C) apply: c_p' = c c_p - s e^{-i phi} c_q ;  c_q' = s e^{i phi} c_p + c c_q
+      for (int k = team; k < npairs; k += nteams) {
+        const double c = sh.pc[k];
+        if (c == 0.0) continue;
+        const int pq = sh.pidx[k];
+        const int p = pq & 0xffff, q = pq >> 16;
+        const double sx = sh.psx[k], sy = sh.psy[k];
         double2* cp = W + (int64_t)p * rows;
         double2* cq = W + (int64_t)q * rows;
-        double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
-        for (int i = lane; i < rows; i += 32) {
+        for (int i = tl; i < rows; i += T) {
           double2 u = cp[i], v = cq[i];
-          a = fma(u.x, u.x, fma(u.y, u.y, a));
-          b = fma(v.x, v.x, fma(v.y, v.y, b));
-          gr = fma(u.x, v.x, fma(u.y, v.y, gr));   // Re(conj(u) v)
-          gi = fma(u.x, v.y, fma(-u.y, v.x, gi));  // Im(conj(u) v)
+          // s e^{-i phi} v = (sx v.x + sy v.y, sx v.y - sy v.x)
+          cp[i] = make_double2(c * u.x - (sx * v.x + sy * v.y), c * u.y - (sx * v.y - sy * v.x));
+          cq[i] = make_double2(c * v.x + (sx * u.x - sy * u.y), c * v.y + (sx * u.y + sy * u.x));
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        gr = warp_sum(gr);
-        gi = warp_sum(gi);
-        double g = sqrt(gr * gr + gi * gi);
-        // a column whose squared norm underflows is treated as zero
-        if (a == 0.0 || b == 0.0 || !(g > tol * sqrt(a) * sqrt(b))) continue;
-        // rotation [[c, s e^{i phi}], [-s e^{-i phi}, c]] zeroing conj(c_p) c_q
-        double zeta = (b - a) / (2.0 * g);
-        double t = fabs(zeta) > 1e100
-                       ? 0.5 / zeta
-                       : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        if (t == 0.0) continue;
-        double c = 1.0 / sqrt(1.0 + t * t);
-        double s = c * t;
-        double er = gr / g, ei = gi / g;  // e^{i phi}
-        // c_p' = c c_p - s e^{-i phi} c_q ;  c_q' = s e^{i phi} c_p + c c_q
-        double2 sm = make_double2(s * er, -s * ei);  // s e^{-i phi}
-        double2 sp = make_double2(s * er, s * ei);   // s e^{+i phi}
-        for (int i = lane; i < rows; i += 32) {
-          double2 u = cp[i], v = cq[i];
-          double2 nu = make_double2(c * u.x - (sm.x * v.x - sm.y * v.y),
-                                    c * u.y - (sm.x * v.y + sm.y * v.x));
-          double2 nv = make_double2(c * v.x + (sp.x * u.x - sp.y * u.y),
-                                    c * v.y + (sp.x * u.y + sp.y * u.x));
-          cp[i] = nu;
-          cq[i] = nv;
-        }
-        if (lane == 0) atomicAdd(&sh.rotated, 1);
       }
       __syncthreads();
     }
@@ -180,11 +230,13 @@ __device__ void sort_columns(const double2* W, int rows, int cols, Shared& sh) {
     if (lane == 0) sh.s2[j] = a;
   }
   __syncthreads();
+  // non-negative doubles order like their bit patterns: compare as integers
+  // (keeps the O(cols^2) ranking off the FP64 pipe)
   for (int i = threadIdx.x; i < cols; i += kThreads) {
-    double v = sh.s2[i];
+    const unsigned long long v = (unsigned long long)__double_as_longlong(sh.s2[i]);
     int rank = 0;
     for (int j = 0; j < cols; ++j) {
-      double u = sh.s2[j];
+      const unsigned long long u = (unsigned long long)__double_as_longlong(sh.s2[j]);
       rank += (u > v) || (u == v && j < i);
     }
     sh.perm[rank] = i;
@@ -490,7 +542,7 @@ __device__ void two_site(const BuildArgs& a, double2* slice, const double* x, co
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) build_kernel(BuildArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) build_kernel(BuildArgs a) {
   __shared__ Shared sh;
   double2* slice = a.ws + (int64_t)blockIdx.x * a.ws_stride;
   const int n = a.n;

@@ -1,15 +1,819 @@
-// Split-precision tensor-core transfer sweep (placeholder until the tcgen05
-// kernel lands): reports that the path is unavailable.
+// Split-precision transfer sweep (Fig. 2) on the tcgen05 tensor cores.
+//
+// Per site k every pair (i, j) updates its environment E (chi^i_k x chi^j_k)
+// in two half-steps, both complex GEMMs:
+//   HS1 (ket side):  T_s[a][b'] = sum_b E[a][b] B_j[s][b][b']
+//   HS2 (bra side):  E'[a'][b'] = sum_{s,a} conj(A_i[s][a][a']) T_s[a][b']
+// A CTA takes one bra i and up to kG kets; HS2 stacks the kets' columns so
+// the bra tensor is read once for all of them.  Operands as GEMM factors:
+//   HS1: D1[(s,b'), a]   = Bt_j[(s,b'), b] . Et[b, a]        (A static, B = E)
+//   HS2: D2[a', (j,b')]  = Ah_i[a', (s,a)] . T[(s,a), (j,b')] (A static, B = T)
+// Every operand is stored K-major in 16-wide K chunks of 8x(16 B) core
+// matrices (no swizzle), as bf16 planes of re and im, each value split into
+// P parts x = x0 + x1 (+ x2), x_{k+1} = bf16(x - x0 - .. - x_k):
+//   P = 2: residual <= 2^-17 |x|; products 00, 01, 10 (order >= 2^-8 kept,
+//          lo*lo dropped), 12 MMAs per 16-wide K chunk for a complex product;
+//   P = 3: exact for any FP32 value; products 00, 01, 10, 02, 11, 20 (order
+//          >= 2^-16 kept), 24 MMAs per chunk.
+// re += Ar Br - Ai Bi (the minus via the A-negate bit), im += Ar Bi + Ai Br,
+// all accumulated in FP32 in TMEM.  The static (per-state) operands Bt/Ah are packed once
+// per batch (tc_pack_kernel); E and T live in a per-CTA global scratch that
+// the epilogue writes (tcgen05.ld -> split -> st.global) and the next GEMM
+// streams back with 1-D bulk copies.  One elected thread keeps a 2-stage
+// mbarrier ring of bulk copies ahead of its MMAs; every wait is bounded in
+// time and reports QK_ERR_TIMEOUT instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "qk_internal.h"
 
 namespace qk {
-void free_tc_cache(qk_mps_batch* b) { b->tc_cache = nullptr; }
-qk_status gram_split(const qk_mps_batch*, const qk_mps_batch*, double*, int64_t, double,
-                     cudaStream_t, int64_t*) {
-  return fail(QK_ERR_INVALID_ARG, "qk_gram: split-precision path not available in this build");
+
+qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
+                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st);
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kG = 4;            // kets per tile
+constexpr int kStages = 2;
+constexpr int kMaxPlanes = 6;
+constexpr int kStageBytes = 128 * 32 * kMaxPlanes;  // 128 rows of one K chunk, all planes
+constexpr int kTmemCols = 256;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;
+
+__host__ __device__ inline int pad16(int x) { return (x + 15) & ~15; }
+__host__ __device__ inline int mrows_of(int rows) { return rows <= 64 ? 64 : 128; }
+__host__ __device__ inline int ntiles_of(int rows) { return rows <= 64 ? 1 : (rows + 127) / 128; }
+
+// element offset of (row, k) in a [kchunk][plane][rows x 16] block
+template <int PL>
+__host__ __device__ inline int64_t blk_off(int row, int k, int plane, int rows) {
+  const int kc = k >> 4, k16 = k & 15;
+  return ((int64_t)kc * PL + plane) * rows * 16 + (row >> 3) * 128 + (k16 >> 3) * 64 + (row & 7) * 8 +
+         (k16 & 7);
 }
-qk_status pairs_split(const qk_mps_batch*, const qk_mps_batch*, const int32_t*, int64_t, double*,
-                      cudaStream_t) {
-  return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: split-precision path not available in this build");
+
+// ---------------------------------------------------------------- packing
+struct PackArgs {
+  const uint64_t* site_ptr;  // [N][n]
+  const int32_t* dims;       // [N][n+1]
+  int n;
+  int store;                 // 1: complex64, 0: complex128
+  const int64_t* bt_off;     // [N][n] byte offsets
+  const int64_t* ah_off;
+  char* arena;
+};
+
+template <int P>
+__device__ inline void splitp(float x, __nv_bfloat16* o) {
+  float r = x;
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    o[i] = __float2bfloat16_rn(r);
+    r -= __bfloat162float(o[i]);
+  }
 }
+
+template <int P>
+__global__ void tc_pack_kernel(PackArgs p) {
+  constexpr int kParts = P, kPlanes = 2 * P;
+  const int s = blockIdx.y, k = blockIdx.x;
+  const int n = p.n;
+  const int c0 = p.dims[(int64_t)s * (n + 1) + k], c1 = p.dims[(int64_t)s * (n + 1) + k + 1];
+  const int p0 = pad16(c0), p1 = pad16(c1);
+  const void* src = (const void*)p.site_ptr[(int64_t)s * n + k];
+  auto val = [&](int q, int a, int b) -> float2 {  // A[q][a][b]
+    int64_t idx = ((int64_t)q * c0 + a) * c1 + b;
+    if (p.store) return reinterpret_cast<const float2*>(src)[idx];
+    double2 v = reinterpret_cast<const double2*>(src)[idx];
+    return make_float2((float)v.x, (float)v.y);
+  };
+  // ket form Bt[(q, b'), b] = A[q][b][b'], rows 2*p1 (padded to the M tile), K = p0
+  {
+    const int rows = 2 * p1;
+    const int mr = mrows_of(rows), nt = ntiles_of(rows);
+    __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.arena + p.bt_off[(int64_t)s * n + k]);
+    const int total = nt * mr * p0;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int R = e / p0, b = e % p0;
+      const int t = R / mr, r = R % mr;
+      float2 v = make_float2(0.f, 0.f);
+      if (R < rows) {
+        const int q = R / p1, bp = R % p1;
+        if (bp < c1 && b < c0) v = val(q, b, bp);
+      }
+      __nv_bfloat16* blk = base + (int64_t)t * (p0 / 16) * kPlanes * mr * 16;
+      __nv_bfloat16 h[kPlanes];
+      splitp<P>(v.x, h);
+      splitp<P>(v.y, h + kParts);
+      for (int pl = 0; pl < kPlanes; ++pl) blk[blk_off<kPlanes>(r, b, pl, mr)] = h[pl];
+    }
+  }
+  // bra form Ah[a', (q, a)] = conj(A[q][a][a']), rows p1 (<= 128), K = 2*p0
+  {
+    const int mr = mrows_of(p1);
+    __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.arena + p.ah_off[(int64_t)s * n + k]);
+    const int total = mr * 2 * p0;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int r = e / (2 * p0), K = e % (2 * p0);
+      const int q = K / p0, a = K % p0;
+      float2 v = make_float2(0.f, 0.f);
+      if (r < c1 && a < c0) {
+        v = val(q, a, r);
+        v.y = -v.y;
+      }
+      __nv_bfloat16 h[kPlanes];
+      splitp<P>(v.x, h);
+      splitp<P>(v.y, h + kParts);
+      for (int pl = 0; pl < kPlanes; ++pl) base[blk_off<kPlanes>(r, K, pl, mr)] = h[pl];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t make_desc(uint32_t saddr) {
+  // K-major, no swizzle: LBO (next core matrix along K) = 128 B,
+  // SBO (next 8-row group) = 256 B, descriptor version 1
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ inline uint32_t make_idesc(int M, int N, int neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg_a << 13) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ inline void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ inline void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(bar)));
+}
+
+__device__ inline unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait on an mbarrier phase; false on timeout
+__device__ inline bool wait_bar(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint32_t done = 0;
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity));
+    if (done) return true;
+    if ((it & 255) == 0) {
+      unsigned long long t = now_ns();
+      if (it == 0)
+        t0 = t;
+      else if (t - t0 > kTimeoutNs)
+        return false;
+    }
+  }
+}
+
+__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ inline void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// split 16 floats into P bf16 planes, two values per cvt.rn.bf16x2
+template <int P>
+__device__ inline void split16(const float* x, uint32_t (*o)[8]) {
+  float r[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r[i] = x[i];
+#pragma unroll
+  for (int part = 0; part < P; ++part) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+      o[part][i] = *reinterpret_cast<uint32_t*>(&b);
+      if (part + 1 < P) {
+        float2 f = __bfloat1622float2(b);
+        r[2 * i] -= f.x;
+        r[2 * i + 1] -= f.y;
+      }
+    }
+  }
+}
+
+// store 16 consecutive K values (re, im) of one row as the 2P bf16 planes
+template <int P>
+__device__ inline void store_row16(__nv_bfloat16* blk, int row, int k, int rows, const float* re,
+                                   const float* im) {
+  constexpr int PL = 2 * P;
+  uint32_t h[PL][8];
+  split16<P>(re, h);
+  split16<P>(im, h + P);
+#pragma unroll
+  for (int pl = 0; pl < PL; ++pl) {
+    uint4* d0 = reinterpret_cast<uint4*>(blk + blk_off<PL>(row, k, pl, rows));
+    uint4* d1 = reinterpret_cast<uint4*>(blk + blk_off<PL>(row, k + 8, pl, rows));
+    *d0 = make_uint4(h[pl][0], h[pl][1], h[pl][2], h[pl][3]);
+    *d1 = make_uint4(h[pl][4], h[pl][5], h[pl][6], h[pl][7]);
+  }
+}
+
+// ---------------------------------------------------------------- overlap kernel
+struct TcArgs {
+  const int32_t* a_dims;
+  const int64_t* a_ah;
+  const char* a_arena;
+  const int32_t* b_dims;
+  const int64_t* b_bt;
+  const char* b_arena;
+  int n;
+  int mode;                  // 0 symmetric full, 1 rectangular full, 2 pair list
+  int64_t n_tiles;
+  const int64_t* row_start;  // modes 0/1: first tile of each bra row
+  int NA, NB;
+  const int32_t* pairs;      // mode 2
+  double* K;
+  int64_t ldk;
+  char* scratch;
+  int64_t scratch_stride;
+  int64_t et_stride;
+  unsigned long long* queue;
+  int* err;
+};
+
+struct __align__(8) TcShared {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t done;
+  uint32_t tmem;
+  int abort;
+  int64_t tile;
+};
+
+// Streams `nchunks` K-chunks of (A block, B block) through the ring and issues
+// the 4 x (split products) MMAs per chunk into TMEM columns [0, N) (re) and
+// [N, 2N) (im).  Called by thread 0 only.  g is the running chunk counter.
+template <int P>
+__device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_bytes, const char* gB,
+                         uint32_t b_bytes, int nchunks, int M, int N, uint32_t& g) {
+  const uint32_t id_pos = make_idesc(M, N, 0), id_neg = make_idesc(M, N, 1);
+  const uint32_t t_re = sh.tmem, t_im = sh.tmem + N;
+  auto produce = [&](int c, uint32_t gi) -> bool {
+    const int slot = gi % kStages;
+    if (gi >= (uint32_t)kStages && !wait_bar(&sh.empty[slot], ((gi / kStages) - 1) & 1)) return false;
+    char* sA = stage + slot * 2 * kStageBytes;
+    char* sB = sA + kStageBytes;
+    expect_tx(&sh.full[slot], a_bytes + b_bytes);
+    bulk_load(sA, gA + (int64_t)c * a_bytes, a_bytes, &sh.full[slot]);
+    bulk_load(sB, gB + (int64_t)c * b_bytes, b_bytes, &sh.full[slot]);
+    return true;
+  };
+  const uint32_t g0 = g;
+  const int look = kStages - 1;
+  for (int c = 0; c < look && c < nchunks; ++c)
+    if (!produce(c, g0 + c)) return false;
+  for (int c = 0; c < nchunks; ++c) {
+    const uint32_t gi = g0 + c;
+    const int slot = gi % kStages;
+    if (!wait_bar(&sh.full[slot], (gi / kStages) & 1)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const char* sA = stage + slot * 2 * kStageBytes;
+    const char* sB = sA + kStageBytes;
+    const uint32_t pa = (uint32_t)M * 32, pb = (uint32_t)N * 32;  // bytes per plane
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    // cross terms (x part, y part) kept
+    constexpr int NT = P == 2 ? 3 : 6;
+    const int xs[6] = {0, 0, 1, 0, 1, 2};
+    const int ys[6] = {0, 1, 0, 2, 1, 0};
+    const uint32_t acc = c > 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const uint64_t ar = make_desc(a0 + xs[t] * pa), ai = make_desc(a0 + (P + xs[t]) * pa);
+      const uint64_t br = make_desc(b0 + ys[t] * pb), bi = make_desc(b0 + (P + ys[t]) * pb);
+      // re += Ar Br - Ai Bi ; im += Ar Bi + Ai Br
+      mma(t_re, ar, br, id_pos, t > 0 || acc);
+      mma(t_re, ai, bi, id_neg, 1);
+      mma(t_im, ar, bi, id_pos, t > 0 || acc);
+      mma(t_im, ai, br, id_pos, 1);
+    }
+    commit(&sh.empty[slot]);
+    if (c + look < nchunks && !produce(c + look, g0 + c + look)) return false;
+  }
+  commit(&sh.done);
+  g = g0 + nchunks;
+  return true;
+}
+
+// lane -> accumulator row for M = 64 / 128 (64: rows 16w..16w+15 sit in the
+// first 16 lanes of warp w)
+__device__ inline int acc_row(int M) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (M == 128) return 32 * w + l;
+  return l < 16 ? 16 * w + l : -1;
+}
+
+__device__ inline void sync_after_epilogue() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
+  constexpr int kPlanes = 2 * P;
+  constexpr int kRowBytes = 32 * kPlanes;
+  extern __shared__ __align__(1024) char dyn[];
+  __shared__ TcShared sh;
+  char* stage = dyn;
+  const int tid = threadIdx.x;
+  const int n = a.n;
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    sh.abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sh.tmem;
+  uint32_t g = 0;           // ring position (thread 0)
+  uint32_t done_phase = 0;  // completed GEMMs (all threads)
+  char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
+  char* T_buf = scr + (int64_t)kG * a.et_stride;
+
+  while (true) {
+    if (tid == 0) sh.tile = (int64_t)atomicAdd(a.queue, 1ull);
+    __syncthreads();
+    const int64_t tile = sh.tile;
+    if (tile >= a.n_tiles || sh.abort) break;
+    // ---- decode the tile: bra i, kets j[0..nk), output slots
+    int i, nk = 0;
+    int jj[kG];
+    int64_t outp[kG];
+    if (a.mode == 2) {
+      i = a.pairs[2 * tile];
+      jj[0] = a.pairs[2 * tile + 1];
+      outp[0] = tile;
+      nk = 1;
+    } else {
+      int lo = 0, hi = a.NA - 1;  // last row with row_start <= tile
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.row_start[mid] <= tile) lo = mid; else hi = mid - 1;
+      }
+      i = lo;
+      const int64_t t_in = tile - a.row_start[i];
+      const int j0 = (a.mode == 0 ? i : 0) + (int)(t_in * kG);
+      for (int q = 0; q < kG && j0 + q < a.NB; ++q) {
+        jj[q] = j0 + q;
+        outp[q] = (int64_t)i * a.ldk + j0 + q;
+        ++nk;
+      }
+    }
+    // ---- E_0 = [1]: Et blocks of 16 x 16 (one chunk), only (0, 0) = 1
+    for (int q = 0; q < nk; ++q) {
+      __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
+      for (int e = tid; e < kPlanes * 16 * 16; e += kThreads) et[e] = __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    if (tid < nk) {
+      __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + tid * a.et_stride);
+      et[blk_off<kPlanes>(0, 0, 0, 16)] = __float2bfloat16_rn(1.f);
+    }
+    sync_after_epilogue();
+    const int32_t* da = a.a_dims + (int64_t)i * (n + 1);
+    for (int k = 0; k < n; ++k) {
+      const int ap = pad16(da[k]), ap1 = pad16(da[k + 1]);
+      int q0 = 0;
+      while (q0 < nk) {
+        // group kets while the stacked columns fit (<= 128)
+        int q1 = q0, ntot = 0;
+        int nb[kG];
+        while (q1 < nk) {
+          const int w = pad16(a.b_dims[(int64_t)jj[q1] * (n + 1) + k + 1]);
+          if (q1 > q0 && ntot + w > 128) break;
+          nb[q1] = ntot;
+          ntot += w;
+          ++q1;
+        }
+        // ---- HS1 for each ket of the group
+        for (int q = q0; q < q1; ++q) {
+          const int32_t* db = a.b_dims + (int64_t)jj[q] * (n + 1);
+          const int bp = pad16(db[k]), bp1 = pad16(db[k + 1]);
+          const int rows = 2 * bp1, mr = mrows_of(rows), nt = ntiles_of(rows);
+          const char* bt = a.b_arena + a.b_bt[(int64_t)jj[q] * n + k];
+          const char* et = scr + q * a.et_stride;
+          for (int t = 0; t < nt; ++t) {
+            if (tid == 0) {
+              const char* gA = bt + (int64_t)t * (bp / 16) * mr * kRowBytes;
+              if (!run_gemm<P>(sh, stage, gA, mr * kRowBytes, et, ap * kRowBytes, bp / 16, mr, ap, g)) {
+                sh.abort = 1;
+                atomicExch(a.err, 1);
+              }
+            }
+            __syncthreads();
+            if (sh.abort) goto finish;
+            if (!wait_bar(&sh.done, done_phase & 1)) {
+              sh.abort = 1;
+              atomicExch(a.err, 1);
+            }
+            ++done_phase;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            {
+              const int r = acc_row(mr);
+              const int R = t * 128 + r;
+              const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
+              __nv_bfloat16* Tb = reinterpret_cast<__nv_bfloat16*>(T_buf);
+              for (int c = 0; c < ap; c += 16) {
+                float re[16], im[16];
+                tmem_ld16(tmem + lane_base + c, re);
+                tmem_ld16(tmem + lane_base + ap + c, im);
+                if (r >= 0 && R < rows) {
+                  const int s = R / bp1, b1 = R % bp1;
+                  store_row16<P>(Tb, nb[q] + b1, s * ap + c, ntot, re, im);
+                }
+              }
+            }
+            sync_after_epilogue();
+            if (sh.abort) goto finish;
+          }
+        }
+        // ---- HS2 for the group
+        {
+          const int mr = mrows_of(ap1);
+          const char* ah = a.a_arena + a.a_ah[(int64_t)i * n + k];
+          if (tid == 0) {
+            if (!run_gemm<P>(sh, stage, ah, mr * kRowBytes, T_buf, ntot * kRowBytes, (2 * ap) / 16, mr, ntot, g)) {
+              sh.abort = 1;
+              atomicExch(a.err, 1);
+            }
+          }
+          __syncthreads();
+          if (sh.abort) goto finish;
+          if (!wait_bar(&sh.done, done_phase & 1)) {
+            sh.abort = 1;
+            atomicExch(a.err, 1);
+          }
+          ++done_phase;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int r = acc_row(mr);
+          const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
+          if (k + 1 < n) {
+            for (int q = q0; q < q1; ++q) {
+              const int bp1 = pad16(a.b_dims[(int64_t)jj[q] * (n + 1) + k + 1]);
+              __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
+              for (int c = 0; c < bp1; c += 16) {
+                float re[16], im[16];
+                tmem_ld16(tmem + lane_base + nb[q] + c, re);
+                tmem_ld16(tmem + lane_base + ntot + nb[q] + c, im);
+                if (r >= 0 && r < ap1) store_row16<P>(et, r, c, ap1, re, im);
+              }
+            }
+          } else {
+            // last site: 1 x 1 environments, z = E[0][0]
+            for (int q = q0; q < q1; ++q) {
+              float re[16], im[16];
+              tmem_ld16(tmem + lane_base + nb[q], re);
+              tmem_ld16(tmem + lane_base + ntot + nb[q], im);
+              if (r == 0) {
+                const double zr = re[0], zi = im[0];
+                const double kv = zr * zr + zi * zi;
+                a.K[outp[q]] = kv;
+                if (a.mode == 0 && jj[q] != i) a.K[(int64_t)jj[q] * a.ldk + i] = kv;
+              }
+            }
+          }
+          sync_after_epilogue();
+          if (sh.abort) goto finish;
+        }
+        q0 = q1;
+      }
+    }
+  }
+finish:
+  __syncthreads();
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// compaction of the entries that go to FP64: K < floor_v or K > ceil_v
+__global__ void select_refine_kernel(const double* K, int64_t ldk, int NA, int NB, int sym, double floor_v,
+                                     double ceil_v, int32_t* pairs, unsigned long long* count,
+                                     unsigned long long cap) {
+  const int64_t total = (int64_t)NA * NB;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / NB), j = (int)(e % NB);
+    if (sym && j < i) continue;
+    const double v = K[(int64_t)i * ldk + j];
+    if (v < floor_v || v > ceil_v) {
+      unsigned long long p = atomicAdd(count, 1ull);
+      if (p < cap) {
+        pairs[2 * p] = i;
+        pairs[2 * p + 1] = j;
+      }
+    }
+  }
+}
+
+// pair-list variant: positions p with K[p] > ceil_v
+__global__ void select_refine_list_kernel(const double* K, const int32_t* pairs, int64_t P, double ceil_v,
+                                          int32_t* sel_pairs, int64_t* sel_pos, unsigned long long* count) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    if (K[p] > ceil_v) {
+      unsigned long long q = atomicAdd(count, 1ull);
+      sel_pairs[2 * q] = pairs[2 * p];
+      sel_pairs[2 * q + 1] = pairs[2 * p + 1];
+      sel_pos[q] = p;
+    }
+  }
+}
+
+__global__ void scatter_kernel(const int32_t* pairs, const double* v, int64_t P, double* K, int64_t ldk, int sym) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = pairs[2 * p], j = pairs[2 * p + 1];
+    K[(int64_t)i * ldk + j] = v[p];
+    if (sym) K[(int64_t)j * ldk + i] = v[p];
+  }
+}
+
+__global__ void scatter_list_kernel(const int64_t* pos, const double* v, int64_t P, double* K) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+    K[pos[p]] = v[p];
+}
+
+// Per-batch packed operands, one arena per split depth (index P - 2).
+struct TcArena {
+  char* arena = nullptr;
+  int64_t* d_bt = nullptr;
+  int64_t* d_ah = nullptr;
+  int64_t bytes = 0;
+};
+struct TcCache {
+  TcArena part[2];
+};
+
+template <int P>
+qk_status ensure_tc_arena(qk_mps_batch* b, cudaStream_t st) {
+  constexpr int kPlanes = 2 * P;
+  if (!b->tc_cache) b->tc_cache = new TcCache();
+  TcArena& c = ((TcCache*)b->tc_cache)->part[P - 2];
+  if (c.arena) return QK_OK;
+  const int n = b->n;
+  const int64_t N = b->N;
+  std::vector<int64_t> bt((size_t)N * n), ah((size_t)N * n);
+  int64_t off = 0;
+  for (int64_t s = 0; s < N; ++s)
+    for (int k = 0; k < n; ++k) {
+      const int c0 = b->h_dims[s * (n + 1) + k], c1 = b->h_dims[s * (n + 1) + k + 1];
+      const int p0 = pad16(c0), p1 = pad16(c1);
+      bt[s * n + k] = off;
+      off += (int64_t)ntiles_of(2 * p1) * mrows_of(2 * p1) * p0 * 2 * kPlanes;
+      ah[s * n + k] = off;
+      off += (int64_t)mrows_of(p1) * 2 * p0 * 2 * kPlanes;
+    }
+  auto bail = [&](cudaError_t e, const char* w) {
+    cudaFree(c.arena);
+    cudaFree(c.d_bt);
+    cudaFree(c.d_ah);
+    c = TcArena();
+    return cuda_fail(e, w);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&c.arena, off)) != cudaSuccess) return bail(e, "cudaMalloc(tc arena)");
+  if ((e = cudaMalloc(&c.d_bt, sizeof(int64_t) * N * n)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&c.d_ah, sizeof(int64_t) * N * n)) != cudaSuccess) return bail(e, "cudaMalloc");
+  cudaMemcpyAsync(c.d_bt, bt.data(), sizeof(int64_t) * N * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c.d_ah, ah.data(), sizeof(int64_t) * N * n, cudaMemcpyHostToDevice, st);
+  PackArgs p;
+  p.site_ptr = b->d_site_ptr;
+  p.dims = b->d_dims;
+  p.n = n;
+  p.store = b->store == QK_STORE_C64 ? 1 : 0;
+  p.bt_off = c.d_bt;
+  p.ah_off = c.d_ah;
+  p.arena = c.arena;
+  for (int64_t s0 = 0; s0 < N; s0 += 65535) {
+    const int64_t cnt = std::min<int64_t>(65535, N - s0);
+    PackArgs q = p;
+    q.site_ptr = p.site_ptr + s0 * n;
+    q.dims = p.dims + s0 * (n + 1);
+    q.bt_off = p.bt_off + s0 * n;
+    q.ah_off = p.ah_off + s0 * n;
+    tc_pack_kernel<P><<<dim3(n, (unsigned)cnt), 256, 0, st>>>(q);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "tc_pack_kernel");
+  // the host offset tables must outlive the asynchronous copies
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "tc_pack_kernel");
+  c.bytes = off;
+  return QK_OK;
+}
+
+template <int P>
+qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, const int32_t* d_pairs,
+                    int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st) {
+  constexpr int kPlanes = 2 * P;
+  qk_status rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(A), st);
+  if (rc != QK_OK) return rc;
+  rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(B), st);
+  if (rc != QK_OK) return rc;
+  const TcArena& ca = ((const TcCache*)A->tc_cache)->part[P - 2];
+  const TcArena& cb = ((const TcCache*)B->tc_cache)->part[P - 2];
+  int dev = 0, sms = 0;
+  QK_CUDA(cudaGetDevice(&dev));
+  QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // tiles
+  std::vector<int64_t> row_start;
+  int64_t n_tiles = 0;
+  if (mode == 2) {
+    n_tiles = P_pairs;
+  } else {
+    row_start.resize(A->N + 1);
+    for (int64_t i = 0; i < A->N; ++i) {
+      row_start[i] = n_tiles;
+      const int64_t cols = mode == 0 ? B->N - i : B->N;
+      n_tiles += (cols + kG - 1) / kG;
+    }
+    row_start[A->N] = n_tiles;
+  }
+  if (n_tiles == 0) return QK_OK;
+  // scratch: kG Et blocks (<= 128 x 128) + T (<= 128 rows x 256 K), bf16 planes
+  const int chi = std::max(A->chi_cap, B->chi_cap);
+  const int cp = pad16(chi);
+  const int64_t et_stride = (int64_t)cp * cp * 2 * kPlanes + 256;
+  const int64_t t_bytes = (int64_t)128 * 2 * cp * 2 * kPlanes;
+  const int64_t stride = ((kG * et_stride + t_bytes) + 1023) & ~int64_t(1023);
+  const int64_t ctas = std::min<int64_t>((int64_t)2 * sms, n_tiles);
+  char* scratch = nullptr;
+  int64_t* d_rs = nullptr;
+  unsigned long long* queue = nullptr;
+  int* err = nullptr;
+  QK_CUDA(cudaMallocAsync(&scratch, stride * ctas, st));
+  QK_CUDA(cudaMallocAsync(&queue, sizeof(unsigned long long), st));
+  QK_CUDA(cudaMallocAsync(&err, sizeof(int), st));
+  QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st));
+  QK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  if (!row_start.empty()) {
+    QK_CUDA(cudaMallocAsync(&d_rs, sizeof(int64_t) * row_start.size(), st));
+    QK_CUDA(cudaMemcpyAsync(d_rs, row_start.data(), sizeof(int64_t) * row_start.size(), cudaMemcpyHostToDevice, st));
+  }
+  TcArgs a;
+  a.a_dims = A->d_dims;
+  a.a_ah = ca.d_ah;
+  a.a_arena = ca.arena;
+  a.b_dims = B->d_dims;
+  a.b_bt = cb.d_bt;
+  a.b_arena = cb.arena;
+  a.n = A->n;
+  a.mode = mode;
+  a.n_tiles = n_tiles;
+  a.row_start = d_rs;
+  a.NA = (int)A->N;
+  a.NB = (int)B->N;
+  a.pairs = d_pairs;
+  a.K = dK;
+  a.ldk = ldk;
+  a.scratch = scratch;
+  a.scratch_stride = stride;
+  a.et_stride = et_stride;
+  a.queue = queue;
+  a.err = err;
+  const int smem = kStages * 2 * kStageBytes;
+  QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  tc_overlap_kernel<P><<<(int)ctas, kThreads, smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(scratch, st);
+  cudaFreeAsync(queue, st);
+  cudaFreeAsync(err, st);
+  if (d_rs) cudaFreeAsync(d_rs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tc_overlap_kernel");
+  if (herr) return fail(QK_ERR_TIMEOUT, "tc_overlap_kernel: a bounded wait ran out");
+  return QK_OK;
+}
+
+qk_status launch_tc_parts(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode,
+                          const int32_t* d_pairs, int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st) {
+  return parts == 3 ? launch_tc<3>(A, B, mode, d_pairs, P_pairs, dK, ldk, st)
+                    : launch_tc<2>(A, B, mode, d_pairs, P_pairs, dK, ldk, st);
+}
+
+}  // namespace
+
+void free_tc_cache(qk_mps_batch* b) {
+  if (!b->tc_cache) return;
+  TcCache* c = (TcCache*)b->tc_cache;
+  for (auto& a : c->part) {
+    cudaFree(a.arena);
+    cudaFree(a.d_bt);
+    cudaFree(a.d_ah);
+  }
+  delete c;
+  b->tc_cache = nullptr;
+}
+
+qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK, int64_t ldk,
+                     double refine_floor, cudaStream_t st, int64_t* n_refined) {
+  const bool sym = (A == B);
+  qk_status rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st);
+  if (rc != QK_OK) return rc;
+  // FP64 re-evaluation of the entries below the floor and above the ceiling
+  const unsigned long long cap = sym ? (unsigned long long)A->N * (A->N + 1) / 2
+                                     : (unsigned long long)A->N * B->N;
+  int32_t* pairs = nullptr;
+  unsigned long long* cnt = nullptr;
+  QK_CUDA(cudaMallocAsync(&pairs, sizeof(int32_t) * 2 * cap, st));
+  QK_CUDA(cudaMallocAsync(&cnt, sizeof(unsigned long long), st));
+  QK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  select_refine_kernel<<<1024, 256, 0, st>>>(dK, ldk, (int)A->N, (int)B->N, sym ? 1 : 0, refine_floor,
+                                             QK_SPLIT_REFINE_ABOVE, pairs, cnt, cap);
+  unsigned long long hc = 0;
+  QK_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  QK_CUDA(cudaStreamSynchronize(st));
+  if (n_refined) *n_refined = (int64_t)hc;
+  if (hc > 0) {
+    double* vals = nullptr;
+    QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
+    rc = overlap_fp64(A, B, pairs, (int64_t)hc, vals, 0, false, st);
+    if (rc == QK_OK) scatter_kernel<<<1024, 256, 0, st>>>(pairs, vals, (int64_t)hc, dK, ldk, sym ? 1 : 0);
+    cudaFreeAsync(vals, st);
+  }
+  cudaFreeAsync(pairs, st);
+  cudaFreeAsync(cnt, st);
+  return rc;
+}
+
+qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
+                      int64_t P, double* dK, cudaStream_t st) {
+  qk_status rc = launch_tc_parts(parts, A, B, 2, d_pairs, P, dK, 0, st);
+  if (rc != QK_OK) return rc;
+  int32_t* sel = nullptr;
+  int64_t* pos = nullptr;
+  unsigned long long* cnt = nullptr;
+  QK_CUDA(cudaMallocAsync(&sel, sizeof(int32_t) * 2 * P, st));
+  QK_CUDA(cudaMallocAsync(&pos, sizeof(int64_t) * P, st));
+  QK_CUDA(cudaMallocAsync(&cnt, sizeof(unsigned long long), st));
+  QK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  select_refine_list_kernel<<<256, 256, 0, st>>>(dK, d_pairs, P, QK_SPLIT_REFINE_ABOVE, sel, pos, cnt);
+  unsigned long long hc = 0;
+  QK_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  QK_CUDA(cudaStreamSynchronize(st));
+  if (hc > 0) {
+    double* vals = nullptr;
+    QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
+    rc = overlap_fp64(A, B, sel, (int64_t)hc, vals, 0, false, st);
+    if (rc == QK_OK) scatter_list_kernel<<<256, 256, 0, st>>>(pos, vals, (int64_t)hc, dK);
+    cudaFreeAsync(vals, st);
+  }
+  cudaFreeAsync(sel, st);
+  cudaFreeAsync(pos, st);
+  cudaFreeAsync(cnt, st);
+  return rc;
+}
+
 }  // namespace qk

@@ -1,0 +1,118 @@
+"""GPU parity of the split-precision tcgen05 transfer sweep.
+
+Bar: |dK| <= 1e-5 absolute against the FP64 oracle on the same stored
+states (the path's stated tolerance); the tests also hold it to a relative
+bound that the bf16 hi/lo split with FP32 accumulation meets (2^-17 per
+operand, n sites)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import mps, overlap, statevector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qk():
+    import paper_2411_09336_gb300 as qk
+    return qk
+
+
+PRECS = ["split", "split_bf16x3"]
+
+
+def ragged_states(count, n, seed, chis=(4, 9, 16, 33), gamma=0.8):
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(count):
+        x = rng.uniform(-1.5, 1.5, n)
+        out.append(mps.build_mps(x, 1 + s % 4, 2, gamma, chis[s % len(chis)], 1e-10).sites)
+    return out
+
+
+def check(K, Kref, rel=2e-3):
+    K = np.asarray(K)
+    assert np.max(np.abs(K - Kref)) <= 1e-5
+    big = Kref > 1e-8
+    assert np.max(np.abs(K[big] - Kref[big]) / Kref[big]) < rel
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_symmetric_ragged(qk, prec):
+    st = ragged_states(23, 14, 9)
+    A = qk.qk_mps_import(st, store="c64")
+    K, _ = qk.qk_gram(A, prec=prec)
+    Kref = overlap.gram([mps.round_sites(s, "c64") for s in st])
+    check(K.cpu().numpy(), Kref)
+    Kn = K.cpu().numpy()
+    assert np.array_equal(Kn, Kn.T)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rectangular_and_pairs(qk, prec):
+    st = ragged_states(17, 12, 4)
+    A = qk.qk_mps_import(st[:5], store="c64")
+    B = qk.qk_mps_import(st[5:], store="c64")
+    K, _ = qk.qk_gram(A, B, prec=prec)
+    r = [mps.round_sites(s, "c64") for s in st]
+    Kref = overlap.gram(r[:5], r[5:])
+    check(K.cpu().numpy(), Kref)
+    pairs = np.array([[0, 0], [4, 11], [2, 7], [2, 7], [3, 1]], dtype=np.int32)
+    kp = qk.qk_gram_pairs(A, B, pairs, prec=prec).cpu().numpy()
+    check(kp, Kref[pairs[:, 0], pairs[:, 1]])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_large_bonds_two_tiles(qk, prec):
+    """chi = 128 bonds: HS1 needs two 128-row tiles and HS2 a full 128-row tile."""
+    rng = np.random.default_rng(5)
+    st = [mps.build_mps(rng.uniform(-1, 1, 16), 8, 2, 1.0, 128, 0.0).sites for _ in range(5)]
+    assert max(A.shape[2] for s in st for A in s) == 128
+    A = qk.qk_mps_import(st, store="c64")
+    K, _ = qk.qk_gram(A, prec=prec)
+    Kref = overlap.gram([mps.round_sites(s, "c64") for s in st])
+    check(K.cpu().numpy(), Kref)
+
+
+def test_tiny_workload_vs_statevector(qk):
+    w = workloads.tiny()
+    A = qk.qk_build_states(w.X, w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+    K, _ = qk.qk_gram(A, prec="split")
+    Kref = statevector.gram(w.X, w.d, w.reps, w.gamma)
+    assert np.max(np.abs(K.cpu().numpy() - Kref)) <= 1e-5
+
+
+def test_c50_split_vs_fp64_and_refine(qk):
+    w = workloads.c50(N=40)
+    A = qk.qk_build_states(w.X, w.d, w.reps, w.gamma, w.chi_max, w.eps)
+    K64, _ = qk.qk_gram(A, prec="fp64")
+    Ks, nref = qk.qk_gram(A, prec="split")
+    Ks_n, K64_n = Ks.cpu().numpy(), K64.cpu().numpy()
+    iu = np.triu_indices(40)
+    ceil = qk.QK_SPLIT_REFINE_ABOVE
+    # entries above the ceiling (the diagonal at least) come from FP64
+    assert nref == int(np.sum(Ks_n[iu] > ceil)) >= 40
+    hi = Ks_n > ceil
+    assert np.array_equal(Ks_n[hi], K64_n[hi])
+    check(Ks_n, K64_n)
+    # refinement: entries below the floor are re-evaluated in FP64 as well
+    floor = float(np.median(K64_n))
+    Kr, nref2 = qk.qk_gram(A, prec="split", refine_floor=floor)
+    Kr_n = Kr.cpu().numpy()
+    low = Ks_n < floor
+    assert nref2 == int(np.sum(low[iu])) + nref
+    assert np.array_equal(Kr_n[low], K64_n[low])
+    assert np.array_equal(Kr_n[~low], Ks_n[~low])
+
+
+def test_c165_sampled_full_size(qk):
+    """Full-size n=165, d=6, chi_max=128 states (the benchmark circuit): the
+    split Gram of a few GPU-built states against FP64 on the same states,
+    and the relative error of the split path on entries below the ceiling."""
+    w = workloads.c165()
+    A = qk.qk_build_states(w.X[:6], w.d, w.reps, w.gamma, w.chi_max, w.eps)
+    K64, _ = qk.qk_gram(A, prec="fp64")
+    for prec, rel in (("split", 5e-3), ("split_bf16x3", 1e-3)):
+        Ks, _ = qk.qk_gram(A, prec=prec)
+        check(Ks.cpu().numpy(), K64.cpu().numpy(), rel=rel)
