@@ -136,6 +136,37 @@ qk_status qk_mps_export(const qk_mps_batch* b, int64_t s, double* re_im,
 qk_status qk_mps_free(qk_mps_batch* b);
 
 /* ------------------------------------------------------------------------
+ * qk_mps_rz_copies - `copies` rotated copies of every state of `src`:
+ * copy c of state s (output index c * N + s) is exp(-i sum_k phi[c][k] Z_k)
+ * applied to |psi_s>, i.e. a final single-qubit Z layer (Eq. 4, Fig. 1a)
+ * contracted into the sites: slice q of site k times exp(-i phi (1 - 2q)).
+ * Bond dimensions are unchanged.  phi: host or device float64
+ * [copies][n].  Synchronises.  Errors: INVALID_ARG, OOM, CUDA.
+ * ---------------------------------------------------------------------- */
+qk_status qk_mps_rz_copies(const qk_mps_batch* src, const double* phi,
+                           int64_t copies, void* stream, qk_mps_batch** out);
+
+/* Serialise a batch to one host blob / rebuild it on the current device.
+ * Blob: int64 header {magic 0x716b6d7073, N, n, store}, int32 bond dims
+ * [N][n+1] (padded to 8 bytes), then every site of every state in the
+ * device layout A[q][a][b] (complex, storage precision), each site padded
+ * to 256 bytes.  qk_mps_blob_bytes gives the size; `blob` for qk_mps_load
+ * may be host (pinned or pageable) or device memory; load issues one copy
+ * of the arena.  Synchronises.  Errors: INVALID_ARG (bad header or size),
+ * OOM, CUDA. */
+qk_status qk_mps_blob_bytes(const qk_mps_batch* b, int64_t* bytes);
+qk_status qk_mps_save(const qk_mps_batch* b, void* blob, int64_t bytes);
+qk_status qk_mps_load(const void* blob, int64_t bytes, void* stream,
+                      qk_mps_batch** out);
+
+/* Device time of the kernels of the last qk_gram / qk_gram_pairs call on
+ * this thread, from CUDA events on the call's stream: the overlap kernel
+ * (tensor-core or FP64 sweep over all pairs), the FP64 re-evaluation, and
+ * the whole call.  Milliseconds; 0 where a part did not run. */
+qk_status qk_last_profile(double* overlap_ms, double* refine_ms,
+                          double* total_ms);
+
+/* ------------------------------------------------------------------------
  * qk_gram - K[i][j] = |<psi(a_i)|psi(b_j)>|^2 for all i < N_A, j < N_B
  * (Eq. 1) by the transfer sweep of Fig. 2.
  *   A, B     batches with equal n.  B == A (same pointer) selects the

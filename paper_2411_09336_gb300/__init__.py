@@ -54,6 +54,11 @@ _sig("qk_mps_export", [_vp, _i64, _vp, _i64])
 _sig("qk_mps_free", [_vp])
 _sig("qk_gram", [_vp, _vp, _vp, _i64, C.c_int, _f64, _vp, C.POINTER(_i64)])
 _sig("qk_gram_pairs", [_vp, _vp, _vp, _i64, _vp, C.c_int, _vp])
+_sig("qk_mps_rz_copies", [_vp, _vp, _i64, _vp, C.POINTER(_vp)])
+_sig("qk_mps_blob_bytes", [_vp, C.POINTER(_i64)])
+_sig("qk_mps_save", [_vp, _vp, _i64])
+_sig("qk_mps_load", [_vp, _i64, _vp, C.POINTER(_vp)])
+_sig("qk_last_profile", [C.POINTER(_f64), C.POINTER(_f64), C.POINTER(_f64)])
 
 
 class QKError(RuntimeError):
@@ -221,3 +226,39 @@ def qk_gram_pairs(A: MPSBatch, B: MPSBatch, pairs, prec: str = "fp64", out=None,
     _check(_lib.qk_gram_pairs(A.handle, B.handle, _ptr(pairs), P, _ptr(out), _PREC[prec],
                               _stream_ptr(stream)), "qk_gram_pairs")
     return out
+
+
+def qk_mps_rz_copies(src: MPSBatch, phi, stream=None) -> MPSBatch:
+    """Copies of every state with a final exp(-i sum_k phi[c, k] Z_k) layer;
+    phi (copies, n) float64; output state c * N + s."""
+    phi = _as_f64(phi)
+    h = _vp()
+    _check(_lib.qk_mps_rz_copies(src.handle, _ptr(phi), phi.shape[0], _stream_ptr(stream), C.byref(h)),
+           "qk_mps_rz_copies")
+    return MPSBatch(h.value)
+
+
+def qk_mps_blob_bytes(b: MPSBatch) -> int:
+    n = _i64()
+    _check(_lib.qk_mps_blob_bytes(b.handle, C.byref(n)), "qk_mps_blob_bytes")
+    return n.value
+
+
+def qk_mps_save(b: MPSBatch, blob) -> None:
+    """Serialise into `blob` (numpy uint8 / torch uint8, host or device)."""
+    nbytes = blob.nbytes if isinstance(blob, np.ndarray) else blob.numel() * blob.element_size()
+    _check(_lib.qk_mps_save(b.handle, _ptr(blob), nbytes), "qk_mps_save")
+
+
+def qk_mps_load(blob, stream=None) -> MPSBatch:
+    nbytes = blob.nbytes if isinstance(blob, np.ndarray) else blob.numel() * blob.element_size()
+    h = _vp()
+    _check(_lib.qk_mps_load(_ptr(blob), nbytes, _stream_ptr(stream), C.byref(h)), "qk_mps_load")
+    return MPSBatch(h.value)
+
+
+def qk_last_profile() -> dict:
+    """Device milliseconds of the last qk_gram / qk_gram_pairs call."""
+    a, b, c = _f64(), _f64(), _f64()
+    _check(_lib.qk_last_profile(C.byref(a), C.byref(b), C.byref(c)), "qk_last_profile")
+    return {"overlap_ms": a.value, "refine_ms": b.value, "total_ms": c.value}

@@ -346,6 +346,11 @@ extern "C" qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, doubl
   if (!valid_prec(prec)) return fail(QK_ERR_INVALID_ARG, "qk_gram: bad precision");
   if (!(refine_floor >= 0.0)) return fail(QK_ERR_INVALID_ARG, "qk_gram: refine_floor must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
+  timer_begin_call();
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, st);
   const bool sym = (A == B);
   const size_t kb = sizeof(double) * (size_t)((A->N - 1) * ldk + B->N);
   double* dK = K;
@@ -380,8 +385,14 @@ extern "C" qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, doubl
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(K D2H)");
   }
   if (owned) cudaFreeAsync(owned, st);
+  cudaEventRecord(t1, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (rc == QK_OK && e != cudaSuccess) rc = cuda_fail(e, "qk_gram");
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess) ms = 0.f;
+  timer_end_call(ms);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
   return rc;
 }
 
@@ -394,6 +405,7 @@ extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
   if (!pairs || !K_out) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: NULL argument");
   if (!valid_prec(prec)) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs: bad precision");
   cudaStream_t st = (cudaStream_t)stream;
+  timer_begin_call();
   // validate the indices on the host
   std::vector<int32_t> hp;
   const int32_t* hsrc = pairs;
@@ -429,5 +441,6 @@ extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
   if (owned_k) cudaFreeAsync(owned_k, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (rc == QK_OK && e != cudaSuccess) rc = cuda_fail(e, "qk_gram_pairs");
+  timer_end_call(0.0);
   return rc;
 }

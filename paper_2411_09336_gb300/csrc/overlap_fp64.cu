@@ -181,10 +181,12 @@ qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32
   a.scratch = scratch;
   a.cap = cap;
   a.queue = queue;
+  timer_mark(false, st);
   if (A->store == QK_STORE_C64)
     overlap_fp64_kernel<float2><<<(int)ctas, kThreads, 0, st>>>(a);
   else
     overlap_fp64_kernel<double2><<<(int)ctas, kThreads, 0, st>>>(a);
+  timer_mark(true, st);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(scratch, st);
   cudaFreeAsync(queue, st);

@@ -723,7 +723,9 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.err = err;
   const int smem = kStages * 2 * kStageBytes;
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  timer_mark(false, st);
   tc_overlap_kernel<P><<<(int)ctas, kThreads, smem, st>>>(a);
+  timer_mark(true, st);
   cudaError_t e = cudaGetLastError();
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -779,7 +781,9 @@ qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, do
   if (hc > 0) {
     double* vals = nullptr;
     QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
+    timer_set_phase(1);
     rc = overlap_fp64(A, B, pairs, (int64_t)hc, vals, 0, false, st);
+    timer_set_phase(0);
     if (rc == QK_OK) scatter_kernel<<<1024, 256, 0, st>>>(pairs, vals, (int64_t)hc, dK, ldk, sym ? 1 : 0);
     cudaFreeAsync(vals, st);
   }
@@ -806,7 +810,9 @@ qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, c
   if (hc > 0) {
     double* vals = nullptr;
     QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
+    timer_set_phase(1);
     rc = overlap_fp64(A, B, sel, (int64_t)hc, vals, 0, false, st);
+    timer_set_phase(0);
     if (rc == QK_OK) scatter_list_kernel<<<256, 256, 0, st>>>(pos, vals, (int64_t)hc, dK);
     cudaFreeAsync(vals, st);
   }

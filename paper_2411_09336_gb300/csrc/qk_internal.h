@@ -70,6 +70,11 @@ struct qk_mps_batch {
 };
 
 namespace qk {
+// kernel timings of the current qk_gram call (see qk_last_profile)
+void timer_begin_call();
+void timer_set_phase(int phase);  // 0: main sweep, 1: FP64 refinement
+void timer_mark(bool end, cudaStream_t st);
+void timer_end_call(double total_ms);
 size_t elem_bytes(qk_store s);
 void free_batch_memory(qk_mps_batch* b);
 void free_tc_cache(qk_mps_batch* b);
