@@ -194,6 +194,34 @@ qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
                         qk_prec prec, void* stream);
 
 /* ------------------------------------------------------------------------
+ * qk_gram_pairs_noalloc - the FP64 pair overlaps of qk_gram_pairs
+ * (QK_PREC_FP64) without any device or host allocation inside the call.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate during the work, e.g. a host application that owns the
+ * whole device memory pool through its own allocator, or a latency-bound
+ * loop that cannot afford the device-wide synchronisation a cudaMalloc /
+ * cudaFree may cause.
+ *   A, B     batches on the current device with equal n and storage
+ *            precision; every bond dimension must be <= 64.
+ *   pairs    device int32 [P][2], indices in range (checked through a fixed
+ *            stack buffer before the launch).
+ *   K_out    device float64 [P].
+ * Scratch is a file-scope device array of 37.7 MB (a 256-byte work counter
+ * plus one 384 KiB slice per CTA for 96 CTAs), which every device that loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, once per
+ * device); make that first call before any stream capture.  Every call
+ * shares the array: the work counter is cleared at the start of each call,
+ * and calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so serialise them.  Synchronises.
+ * Errors: INVALID_ARG (bond dimension above 64, host pointers, index out of
+ * range, mismatched batches), CUDA.
+ * ---------------------------------------------------------------------- */
+qk_status qk_gram_pairs_noalloc(const qk_mps_batch* A, const qk_mps_batch* B,
+                                const int32_t* pairs, int64_t P, double* K_out,
+                                void* stream);
+
+/* ------------------------------------------------------------------------
  * Learned surrogate for log K (not in the paper).  A 3-layer MLP
  *   f -> ReLU(W1 f + b1) -> ReLU(W2 h + b2) -> w3 . h + b3
  * on the symmetric pair features f(x, y) = [(x - y)^2, (x + y)/2] (2n values),

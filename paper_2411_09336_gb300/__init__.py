@@ -59,6 +59,7 @@ _sig("qk_mps_blob_bytes", [_vp, C.POINTER(_i64)])
 _sig("qk_mps_save", [_vp, _vp, _i64])
 _sig("qk_mps_load", [_vp, _i64, _vp, C.POINTER(_vp)])
 _sig("qk_last_profile", [C.POINTER(_f64), C.POINTER(_f64), C.POINTER(_f64)])
+_sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
 
 
 class QKError(RuntimeError):
@@ -262,3 +263,12 @@ def qk_last_profile() -> dict:
     a, b, c = _f64(), _f64(), _f64()
     _check(_lib.qk_last_profile(C.byref(a), C.byref(b), C.byref(c)), "qk_last_profile")
     return {"overlap_ms": a.value, "refine_ms": b.value, "total_ms": c.value}
+
+
+def qk_gram_pairs_noalloc(A: MPSBatch, B: MPSBatch, pairs, out, stream=None):
+    """FP64 pair overlaps into the caller's device buffer `out` with no
+    allocation inside the library call (bond dimensions <= 64; pairs and out
+    must be CUDA tensors).  See include/qk.h for the shared-scratch rules."""
+    _check(_lib.qk_gram_pairs_noalloc(A.handle, B.handle, _ptr(pairs), pairs.shape[0], _ptr(out),
+                                      _stream_ptr(stream)), "qk_gram_pairs_noalloc")
+    return out

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "qk_internal.h"
@@ -195,3 +196,104 @@ qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32
 }
 
 }  // namespace qk
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 pair overlaps (qk_gram_pairs_noalloc).
+// Its scratch is the file-scope array below instead of cudaMallocAsync
+// buffers: one 256-byte control block (work counter) followed by one
+// E / T / E' slice per CTA, sized for bond dimensions up to kNoAllocChi and
+// kNoAllocCtas resident CTAs (37.7 MB, held by every device that loads the
+// library until the process exits).
+namespace qk {
+namespace {
+
+constexpr int kNoAllocChi = 64;
+constexpr int kNoAllocCtas = 96;
+constexpr int64_t kNoAllocCap = 2LL * kNoAllocChi * kNoAllocChi;          // double2 per buffer
+constexpr int64_t kNoAllocCtl = 16;                                       // double2 = 256 bytes
+constexpr int64_t kNoAllocElems = kNoAllocCtl + kNoAllocCtas * 3 * kNoAllocCap;
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (host code may only use the symbol through cudaGetSymbolAddress).
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kMaxDevices] = {};
+
+qk_status noalloc_scratch(int dev, double2** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<double2*>(g_noalloc_ptr[dev]);
+  return QK_OK;
+}
+
+}  // namespace
+}  // namespace qk
+
+extern "C" qk_status qk_gram_pairs_noalloc(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* pairs,
+                                           int64_t P, double* K_out, void* stream) {
+  using namespace qk;
+  if (!A || !B) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: NULL batch");
+  if (A->n != B->n) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: batches differ in n");
+  if (A->store != B->store) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: batches differ in storage precision");
+  if (P < 0 || P >= ((int64_t)1 << 31)) return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: P out of range");
+  if (P == 0) return QK_OK;
+  if (A->chi_cap > kNoAllocChi || B->chi_cap > kNoAllocChi)
+    return fail(QK_ERR_INVALID_ARG,
+                "qk_gram_pairs_noalloc: a bond dimension exceeds 64, the limit of the static scratch "
+                "(use qk_gram_pairs)");
+  if (!pairs || !K_out || !is_device_ptr(pairs) || !is_device_ptr(K_out))
+    return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: pairs and K_out must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  QK_CUDA(cudaGetDevice(&dev));
+  if (dev != A->device || dev != B->device)
+    return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: batches live on another device");
+  double2* scratch = nullptr;
+  qk_status rc = noalloc_scratch(dev, &scratch);
+  if (rc != QK_OK) return rc;
+  // index check through a fixed stack buffer (no allocation)
+  int32_t chunk[2 * 2048];
+  for (int64_t p0 = 0; p0 < P; p0 += 2048) {
+    const int64_t cnt = std::min<int64_t>(2048, P - p0);
+    QK_CUDA(cudaMemcpyAsync(chunk, pairs + 2 * p0, sizeof(int32_t) * 2 * cnt, cudaMemcpyDeviceToHost, st));
+    QK_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q = 0; q < cnt; ++q)
+      if (chunk[2 * q] < 0 || chunk[2 * q] >= A->N || chunk[2 * q + 1] < 0 || chunk[2 * q + 1] >= B->N)
+        return fail(QK_ERR_INVALID_ARG, "qk_gram_pairs_noalloc: pair index out of range");
+  }
+  int sms = 0;
+  QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // the work counter starts at zero on every call
+  QK_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double2) * kNoAllocCtl, st));
+  PairArgs a;
+  a.a_ptr = A->d_site_ptr;
+  a.a_dims = A->d_dims;
+  a.b_ptr = B->d_site_ptr;
+  a.b_dims = B->d_dims;
+  a.n = A->n;
+  a.pairs = pairs;
+  a.P = P;
+  a.K = K_out;
+  a.ldk = 0;
+  a.sym = 0;
+  a.scratch = scratch + kNoAllocCtl;
+  a.cap = kNoAllocCap;
+  a.queue = reinterpret_cast<int*>(scratch);
+  const int ctas = (int)std::min<int64_t>(std::min(kNoAllocCtas, 4 * sms), P);
+  if (A->store == QK_STORE_C64)
+    overlap_fp64_kernel<float2><<<ctas, kThreads, 0, st>>>(a);
+  else
+    overlap_fp64_kernel<double2><<<ctas, kThreads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "qk_gram_pairs_noalloc");
+  return QK_OK;
+}
