@@ -241,6 +241,10 @@ qk_status qk_surrogate_free(qk_surrogate* net);
 int64_t qk_surrogate_param_count(const qk_surrogate* net);
 qk_status qk_surrogate_get_params(const qk_surrogate* net, float* params);
 qk_status qk_surrogate_set_params(qk_surrogate* net, const float* params);
+/* Arithmetic of the products: on (default) rounds every GEMM operand to bf16
+ * (FP32 accumulation); off keeps FP32 operands (used to check the kernels
+ * against an FP64 reference without the bf16 rounding). */
+qk_status qk_surrogate_set_bf16(qk_surrogate* net, int32_t on);
 /* Target standardisation: the network fits (t - mean) / scale. */
 qk_status qk_surrogate_set_target_scale(qk_surrogate* net, double mean,
                                         double scale);

@@ -272,3 +272,127 @@ def qk_gram_pairs_noalloc(A: MPSBatch, B: MPSBatch, pairs, out, stream=None):
     _check(_lib.qk_gram_pairs_noalloc(A.handle, B.handle, _ptr(pairs), pairs.shape[0], _ptr(out),
                                       _stream_ptr(stream)), "qk_gram_pairs_noalloc")
     return out
+
+
+_sig("qk_surrogate_create", [_i32, _i32, _u64, C.POINTER(_vp)])
+_sig("qk_surrogate_free", [_vp])
+_sig("qk_surrogate_param_count", [_vp], _i64)
+_sig("qk_surrogate_get_params", [_vp, _vp])
+_sig("qk_surrogate_set_params", [_vp, _vp])
+_sig("qk_surrogate_set_bf16", [_vp, _i32])
+_sig("qk_surrogate_set_target_scale", [_vp, _f64, _f64])
+_sig("qk_surrogate_loss_grad", [_vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _vp, C.POINTER(_f64), _vp])
+_sig("qk_surrogate_train", [_vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _i32, _i32, _f32, _u64, _vp,
+                            C.POINTER(_f64)])
+_sig("qk_surrogate_predict", [_vp, _vp, _i64, _vp, _i64, _i32, _vp, _i64, _vp, _vp])
+_sig("qk_surrogate_calibrate", [_vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _f64, _i32, _vp])
+_sig("qk_surrogate_bins", [_vp, C.POINTER(_i32), _vp, _vp])
+_sig("qk_gram_surrogate", [_vp, _vp, _vp, _vp, _vp, _f64, _vp, _i64, _vp, C.c_int, _vp, C.POINTER(_i64)])
+
+
+class Surrogate:
+    """Handle of the library's MLP surrogate for log K (qk_surrogate*)."""
+
+    def __init__(self, in_dim: int, hidden: int = 512, seed: int = 0):
+        h = _vp()
+        _check(_lib.qk_surrogate_create(in_dim, hidden, seed, C.byref(h)), "qk_surrogate_create")
+        self._h = h
+        self.in_dim, self.hidden = in_dim, hidden
+
+    @property
+    def handle(self):
+        return self._h
+
+    def param_count(self) -> int:
+        return int(_lib.qk_surrogate_param_count(self._h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(_lib.qk_surrogate_get_params(self._h, out.ctypes.data), "qk_surrogate_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(_lib.qk_surrogate_set_params(self._h, p.ctypes.data), "qk_surrogate_set_params")
+
+    def set_bf16(self, on: bool):
+        _check(_lib.qk_surrogate_set_bf16(self._h, 1 if on else 0), "qk_surrogate_set_bf16")
+
+    def set_target_scale(self, mean: float, scale: float):
+        _check(_lib.qk_surrogate_set_target_scale(self._h, float(mean), float(scale)), "qk_surrogate_set_target_scale")
+
+    def loss_grad(self, Xa, Xb, pairs, target, stream=None):
+        Xa, Xb = _as_f64(Xa), _as_f64(Xb)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        target = _as_f64(target)
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        loss = _f64()
+        _check(_lib.qk_surrogate_loss_grad(self._h, _ptr(Xa), Xa.shape[0], _ptr(Xb), Xb.shape[0], Xa.shape[1],
+                                           _ptr(pairs), _ptr(target), len(pairs), g.ctypes.data, C.byref(loss),
+                                           _stream_ptr(stream)), "qk_surrogate_loss_grad")
+        return loss.value, g
+
+    def train(self, Xa, Xb, pairs, target, epochs=10, batch=2048, lr=1e-3, seed=0, stream=None) -> float:
+        Xa, Xb = _as_f64(Xa), _as_f64(Xb)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        target = _as_f64(target)
+        loss = _f64()
+        _check(_lib.qk_surrogate_train(self._h, _ptr(Xa), Xa.shape[0], _ptr(Xb), Xb.shape[0], Xa.shape[1],
+                                       _ptr(pairs), _ptr(target), len(pairs), epochs, batch, float(lr), seed,
+                                       _stream_ptr(stream), C.byref(loss)), "qk_surrogate_train")
+        return loss.value
+
+    def predict(self, Xa, Xb, pairs, stream=None) -> np.ndarray:
+        Xa, Xb = _as_f64(Xa), _as_f64(Xb)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        y = np.zeros(len(pairs))
+        _check(_lib.qk_surrogate_predict(self._h, _ptr(Xa), Xa.shape[0], _ptr(Xb), Xb.shape[0], Xa.shape[1],
+                                         _ptr(pairs), len(pairs), y.ctypes.data, _stream_ptr(stream)),
+               "qk_surrogate_predict")
+        return y
+
+    def calibrate(self, Xa, Xb, pairs, truth, alpha=0.05, n_bins=8, stream=None):
+        Xa, Xb = _as_f64(Xa), _as_f64(Xb)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        truth = _as_f64(truth)
+        _check(_lib.qk_surrogate_calibrate(self._h, _ptr(Xa), Xa.shape[0], _ptr(Xb), Xb.shape[0], Xa.shape[1],
+                                           _ptr(pairs), _ptr(truth), len(pairs), float(alpha), n_bins,
+                                           _stream_ptr(stream)), "qk_surrogate_calibrate")
+
+    def bins(self):
+        nb = _i32()
+        _check(_lib.qk_surrogate_bins(self._h, C.byref(nb), None, None), "qk_surrogate_bins")
+        e = np.zeros(nb.value + 1)
+        b = np.zeros(nb.value)
+        _check(_lib.qk_surrogate_bins(self._h, C.byref(nb), e.ctypes.data, b.ctypes.data), "qk_surrogate_bins")
+        return e, b
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.qk_surrogate_free(self._h)
+            self._h = _vp(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def qk_surrogate_create(in_dim: int, hidden: int = 512, seed: int = 0) -> Surrogate:
+    return Surrogate(in_dim, hidden, seed)
+
+
+def qk_gram_surrogate(net: Surrogate, A: MPSBatch, B: MPSBatch, Xa, Xb, tol: float, prec: str = "split",
+                      out=None, stream=None):
+    """K block (N_A x N_B) with surrogate predictions where the calibrated
+    bound <= tol and exact overlaps elsewhere.  Returns (K, accepted, n)."""
+    import torch
+    Xa, Xb = _as_f64(Xa), _as_f64(Xb)
+    if out is None:
+        out = torch.empty((A.N, B.N), dtype=torch.float64, device="cuda")
+    acc = torch.empty((A.N, B.N), dtype=torch.uint8, device="cuda")
+    na = _i64()
+    _check(_lib.qk_gram_surrogate(net.handle, A.handle, B.handle, _ptr(Xa), _ptr(Xb), float(tol), _ptr(out), B.N,
+                                  _ptr(acc), _PREC[prec], _stream_ptr(stream), C.byref(na)), "qk_gram_surrogate")
+    return out, acc, na.value

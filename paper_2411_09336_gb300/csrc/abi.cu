@@ -72,7 +72,8 @@ qk_status build_states_device(const double* dX, int64_t N, int n, int d, int rep
                               int chi_max, double eps, qk_store store, int32_t* rank_trace,
                               cudaStream_t st, qk_mps_batch* out);
 qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
-                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st);
+                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st,
+                       int ctas_per_sm = 4);
 qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK,
                      int64_t ldk, double refine_floor, cudaStream_t st, int64_t* n_refined);
 qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B,
@@ -444,3 +445,12 @@ extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
   timer_end_call(0.0);
   return rc;
 }
+
+namespace qk {
+// exact overlaps of a device pair list into a device vector (surrogate fallback)
+qk_status gram_pairs_exact(qk_prec prec, const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
+                           int64_t P, double* dK, cudaStream_t st) {
+  if (prec == QK_PREC_FP64) return overlap_fp64(A, B, d_pairs, P, dK, 0, false, st);
+  return pairs_split(split_parts(prec), A, B, d_pairs, P, dK, st);
+}
+}  // namespace qk

@@ -153,16 +153,18 @@ __global__ void __launch_bounds__(kThreads) overlap_fp64_kernel(PairArgs a) {
 }  // namespace
 
 // Contract the listed pairs in FP64.  ldk > 0 writes K[i*ldk + j] (mirrored
-// when sym), ldk == 0 writes K[p].
+// when sym), ldk == 0 writes K[p].  ctas_per_sm bounds the grid (1 leaves
+// room for a concurrent tensor-core kernel on every SM).
 qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
-                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st) {
+                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st,
+                       int ctas_per_sm) {
   if (P == 0) return QK_OK;
   int dev = 0, sms = 0;
   QK_CUDA(cudaGetDevice(&dev));
   QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int chi = std::max(A->chi_cap, B->chi_cap);
   int64_t cap = 2LL * chi * chi;
-  int64_t ctas = std::min<int64_t>((int64_t)sms * 4, P);
+  int64_t ctas = std::min<int64_t>((int64_t)sms * ctas_per_sm, P);
   double2* scratch = nullptr;
   int* queue = nullptr;
   QK_CUDA(cudaMallocAsync(&scratch, sizeof(double2) * 3 * cap * ctas, st));

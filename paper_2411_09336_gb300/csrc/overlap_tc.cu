@@ -33,7 +33,8 @@
 namespace qk {
 
 qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
-                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st);
+                       int64_t P, double* dK, int64_t ldk, bool sym, cudaStream_t st,
+                       int ctas_per_sm = 4);
 
 namespace {
 
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
       }
       i = lo;
       const int64_t t_in = tile - a.row_start[i];
-      const int j0 = (a.mode == 0 ? i : 0) + (int)(t_in * kG);
+      const int j0 = (a.mode == 0 ? i + 1 : 0) + (int)(t_in * kG);
       for (int q = 0; q < kG && j0 + q < a.NB; ++q) {
         jj[q] = j0 + q;
         outp[q] = (int64_t)i * a.ldk + j0 + q;
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
                 const double zr = re[0], zi = im[0];
                 const double kv = zr * zr + zi * zi;
                 a.K[outp[q]] = kv;
-                if (a.mode == 0 && jj[q] != i) a.K[(int64_t)jj[q] * a.ldk + i] = kv;
+                if (a.mode == 0) a.K[(int64_t)jj[q] * a.ldk + i] = kv;
               }
             }
           }
@@ -547,7 +548,7 @@ __global__ void select_refine_kernel(const double* K, int64_t ldk, int NA, int N
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / NB), j = (int)(e % NB);
-    if (sym && j < i) continue;
+    if (sym && j <= i) continue;  // the diagonal is already FP64
     const double v = K[(int64_t)i * ldk + j];
     if (v < floor_v || v > ceil_v) {
       unsigned long long p = atomicAdd(count, 1ull);
@@ -674,7 +675,8 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
     row_start.resize(A->N + 1);
     for (int64_t i = 0; i < A->N; ++i) {
       row_start[i] = n_tiles;
-      const int64_t cols = mode == 0 ? B->N - i : B->N;
+      // symmetric: strict upper triangle (the diagonal is contracted in FP64)
+      const int64_t cols = mode == 0 ? B->N - i - 1 : B->N;
       n_tiles += (cols + kG - 1) / kG;
     }
     row_start[A->N] = n_tiles;
@@ -762,9 +764,44 @@ void free_tc_cache(qk_mps_batch* b) {
 qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK, int64_t ldk,
                      double refine_floor, cudaStream_t st, int64_t* n_refined) {
   const bool sym = (A == B);
-  qk_status rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st);
+  int64_t n_diag = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_diag = nullptr;
+  int32_t* dpairs = nullptr;
+  qk_status rc = QK_OK;
+  if (sym) {
+    // The diagonal (K_ii ~ 1, above the FP64 ceiling by construction) runs in
+    // FP64 on a second stream, one CTA per SM, while the tensor-core kernel
+    // contracts the strict upper triangle: the FP64 pipe and the tensor pipe
+    // work at the same time.
+    n_diag = A->N;
+    std::vector<int32_t> hp(2 * n_diag);
+    for (int64_t i = 0; i < n_diag; ++i) hp[2 * i] = hp[2 * i + 1] = (int32_t)i;
+    QK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    QK_CUDA(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+    QK_CUDA(cudaEventCreateWithFlags(&ev_diag, cudaEventDisableTiming));
+    QK_CUDA(cudaEventRecord(ev_ready, st));
+    QK_CUDA(cudaStreamWaitEvent(side, ev_ready, 0));
+    QK_CUDA(cudaMallocAsync(&dpairs, sizeof(int32_t) * 2 * n_diag, side));
+    QK_CUDA(cudaMemcpyAsync(dpairs, hp.data(), sizeof(int32_t) * 2 * n_diag, cudaMemcpyHostToDevice, side));
+    timer_set_phase(1);
+    rc = overlap_fp64(A, A, dpairs, n_diag, dK, ldk, false, side, 1);
+    timer_set_phase(0);
+    cudaFreeAsync(dpairs, side);
+    cudaEventRecord(ev_diag, side);
+    // hp may go: a pageable host-to-device copy has staged it on return
+  }
+  if (rc == QK_OK) rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st);
+  if (sym) {
+    cudaStreamWaitEvent(st, ev_diag, 0);
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(ev_ready);
+    cudaEventDestroy(ev_diag);
+    cudaStreamDestroy(side);
+  }
   if (rc != QK_OK) return rc;
-  // FP64 re-evaluation of the entries below the floor and above the ceiling
+  // FP64 re-evaluation of the off-diagonal entries below the floor and above
+  // the ceiling
   const unsigned long long cap = sym ? (unsigned long long)A->N * (A->N + 1) / 2
                                      : (unsigned long long)A->N * B->N;
   int32_t* pairs = nullptr;
@@ -777,7 +814,7 @@ qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, do
   unsigned long long hc = 0;
   QK_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
   QK_CUDA(cudaStreamSynchronize(st));
-  if (n_refined) *n_refined = (int64_t)hc;
+  if (n_refined) *n_refined = (int64_t)hc + n_diag;
   if (hc > 0) {
     double* vals = nullptr;
     QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
