@@ -41,14 +41,34 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kG = 4;            // kets per tile
 constexpr int kStages = 2;
-constexpr int kMaxPlanes = 6;
-constexpr int kStageBytes = 128 * 32 * kMaxPlanes;  // 128 rows of one K chunk, all planes
-constexpr int kTmemCols = 256;
+constexpr int kNMax = 64;       // N of one MMA: re and im accumulators fill 2 x 64 TMEM columns
+constexpr int kTmemCols = 128;  // four CTAs share an SM's 512 columns
+template <int P>
+struct Stage {
+  static constexpr int A = 128 * 32 * 2 * P;    // 128 rows of one 16-wide K chunk, all planes
+  static constexpr int B = kNMax * 32 * 2 * P;  // up to 64 rows
+  static constexpr int bytes = A + B;
+  static constexpr int ctas_per_sm = P == 2 ? 4 : 3;
+};
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 
 __host__ __device__ inline int pad16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int mrows_of(int rows) { return rows <= 64 ? 64 : 128; }
 __host__ __device__ inline int ntiles_of(int rows) { return rows <= 64 ? 1 : (rows + 127) / 128; }
+// rows stored for M tile t of a static operand with `rows` rows (no padding)
+__host__ __device__ inline int tile_rows(int rows, int t) { return rows - 128 * t < 128 ? rows - 128 * t : 128; }
+
+// element offset of (row, k) in a dynamic B operand: [kchunk][64-row tile]
+// [plane][rows_t x 16], rows_t = min(64, rows - 64 t), so that the rows of
+// one N slice of one chunk form one contiguous block
+template <int PL>
+__host__ __device__ inline int64_t dyn_off(int row, int k, int plane, int rows) {
+  const int kc = k >> 4, k16 = k & 15;
+  const int t = row >> 6, r = row & 63;
+  const int rows_t = min(kNMax, rows - kNMax * t);
+  return (int64_t)kc * PL * rows * 16 + (int64_t)t * PL * kNMax * 16 + (int64_t)plane * rows_t * 16 +
+         (r >> 3) * 128 + (k16 >> 3) * 64 + (r & 7) * 8 + (k16 & 7);
+}
 
 // element offset of (row, k) in a [kchunk][plane][rows x 16] block
 template <int PL>
@@ -93,32 +113,30 @@ __global__ void tc_pack_kernel(PackArgs p) {
     double2 v = reinterpret_cast<const double2*>(src)[idx];
     return make_float2((float)v.x, (float)v.y);
   };
-  // ket form Bt[(q, b'), b] = A[q][b][b'], rows 2*p1 (padded to the M tile), K = p0
+  // ket form Bt[(q, b'), b] = A[q][b][b'], rows 2*p1 in M tiles of 128 rows
+  // stored without padding rows (tile t holds tile_rows(rows, t) rows), K = p0
   {
     const int rows = 2 * p1;
-    const int mr = mrows_of(rows), nt = ntiles_of(rows);
     __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.arena + p.bt_off[(int64_t)s * n + k]);
-    const int total = nt * mr * p0;
+    const int total = rows * p0;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int R = e / p0, b = e % p0;
-      const int t = R / mr, r = R % mr;
+      const int t = R / 128, r = R % 128;
+      const int rt = tile_rows(rows, t);
       float2 v = make_float2(0.f, 0.f);
-      if (R < rows) {
-        const int q = R / p1, bp = R % p1;
-        if (bp < c1 && b < c0) v = val(q, b, bp);
-      }
-      __nv_bfloat16* blk = base + (int64_t)t * (p0 / 16) * kPlanes * mr * 16;
+      const int q = R / p1, bp = R % p1;
+      if (bp < c1 && b < c0) v = val(q, b, bp);
+      __nv_bfloat16* blk = base + (int64_t)t * 128 * p0 * kPlanes;
       __nv_bfloat16 h[kPlanes];
       splitp<P>(v.x, h);
       splitp<P>(v.y, h + kParts);
-      for (int pl = 0; pl < kPlanes; ++pl) blk[blk_off<kPlanes>(r, b, pl, mr)] = h[pl];
+      for (int pl = 0; pl < kPlanes; ++pl) blk[blk_off<kPlanes>(r, b, pl, rt)] = h[pl];
     }
   }
   // bra form Ah[a', (q, a)] = conj(A[q][a][a']), rows p1 (<= 128), K = 2*p0
   {
-    const int mr = mrows_of(p1);
     __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(p.arena + p.ah_off[(int64_t)s * n + k]);
-    const int total = mr * 2 * p0;
+    const int total = p1 * 2 * p0;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
       const int r = e / (2 * p0), K = e % (2 * p0);
       const int q = K / p0, a = K % p0;
@@ -130,7 +148,7 @@ __global__ void tc_pack_kernel(PackArgs p) {
       __nv_bfloat16 h[kPlanes];
       splitp<P>(v.x, h);
       splitp<P>(v.y, h + kParts);
-      for (int pl = 0; pl < kPlanes; ++pl) base[blk_off<kPlanes>(r, K, pl, mr)] = h[pl];
+      for (int pl = 0; pl < kPlanes; ++pl) base[blk_off<kPlanes>(r, K, pl, p1)] = h[pl];
     }
   }
 }
@@ -190,12 +208,30 @@ __device__ inline bool wait_bar(uint64_t* bar, uint32_t parity) {
   }
 }
 
-__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// L2 policies: streamed static operands go first, the per-CTA E/T scratch last
+__device__ inline uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ inline uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
           smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
+}
+
+__device__ inline void st_v4_last(void* p, uint4 v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w), "l"(policy)
+               : "memory");
 }
 
 __device__ inline void expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -239,17 +275,16 @@ __device__ inline void split16(const float* x, uint32_t (*o)[8]) {
 // store 16 consecutive K values (re, im) of one row as the 2P bf16 planes
 template <int P>
 __device__ inline void store_row16(__nv_bfloat16* blk, int row, int k, int rows, const float* re,
-                                   const float* im) {
+                                   const float* im, uint64_t policy) {
   constexpr int PL = 2 * P;
   uint32_t h[PL][8];
   split16<P>(re, h);
   split16<P>(im, h + P);
 #pragma unroll
   for (int pl = 0; pl < PL; ++pl) {
-    uint4* d0 = reinterpret_cast<uint4*>(blk + blk_off<PL>(row, k, pl, rows));
-    uint4* d1 = reinterpret_cast<uint4*>(blk + blk_off<PL>(row, k + 8, pl, rows));
-    *d0 = make_uint4(h[pl][0], h[pl][1], h[pl][2], h[pl][3]);
-    *d1 = make_uint4(h[pl][4], h[pl][5], h[pl][6], h[pl][7]);
+    st_v4_last(blk + dyn_off<PL>(row, k, pl, rows), make_uint4(h[pl][0], h[pl][1], h[pl][2], h[pl][3]), policy);
+    st_v4_last(blk + dyn_off<PL>(row, k + 8, pl, rows), make_uint4(h[pl][4], h[pl][5], h[pl][6], h[pl][7]),
+               policy);
   }
 }
 
@@ -264,7 +299,7 @@ struct TcArgs {
   int n;
   int mode;                  // 0 symmetric full, 1 rectangular full, 2 pair list
   int64_t n_tiles;
-  const int64_t* row_start;  // modes 0/1: first tile of each bra row
+  const int32_t* tiles;      // modes 0/1: (bra i, first ket j0) per tile, banded order
   int NA, NB;
   const int32_t* pairs;      // mode 2
   double* K;
@@ -289,18 +324,20 @@ struct __align__(8) TcShared {
 // the 4 x (split products) MMAs per chunk into TMEM columns [0, N) (re) and
 // [N, 2N) (im).  Called by thread 0 only.  g is the running chunk counter.
 template <int P>
-__device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_bytes, const char* gB,
-                         uint32_t b_bytes, int nchunks, int M, int N, uint32_t& g) {
+__device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_bytes, int a_rows, const char* gB,
+                         uint32_t b_bytes, int64_t b_stride, int nchunks, int M, int N, uint32_t& g, uint64_t pol_a,
+                         uint64_t pol_b) {
+  constexpr int kStageA = Stage<P>::A, kStageBytes = Stage<P>::bytes;
   const uint32_t id_pos = make_idesc(M, N, 0), id_neg = make_idesc(M, N, 1);
   const uint32_t t_re = sh.tmem, t_im = sh.tmem + N;
   auto produce = [&](int c, uint32_t gi) -> bool {
     const int slot = gi % kStages;
     if (gi >= (uint32_t)kStages && !wait_bar(&sh.empty[slot], ((gi / kStages) - 1) & 1)) return false;
-    char* sA = stage + slot * 2 * kStageBytes;
-    char* sB = sA + kStageBytes;
+    char* sA = stage + slot * kStageBytes;
+    char* sB = sA + kStageA;
     expect_tx(&sh.full[slot], a_bytes + b_bytes);
-    bulk_load(sA, gA + (int64_t)c * a_bytes, a_bytes, &sh.full[slot]);
-    bulk_load(sB, gB + (int64_t)c * b_bytes, b_bytes, &sh.full[slot]);
+    bulk_load(sA, gA + (int64_t)c * a_bytes, a_bytes, &sh.full[slot], pol_a);
+    bulk_load(sB, gB + (int64_t)c * b_stride, b_bytes, &sh.full[slot], pol_b);
     return true;
   };
   const uint32_t g0 = g;
@@ -312,9 +349,11 @@ __device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_b
     const int slot = gi % kStages;
     if (!wait_bar(&sh.full[slot], (gi / kStages) & 1)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const char* sA = stage + slot * 2 * kStageBytes;
-    const char* sB = sA + kStageBytes;
-    const uint32_t pa = (uint32_t)M * 32, pb = (uint32_t)N * 32;  // bytes per plane
+    const char* sA = stage + slot * kStageBytes;
+    const char* sB = sA + kStageA;
+    // bytes per plane: A is stored with a_rows rows (rows of the M tile past
+    // a_rows read other data and only feed accumulator rows that are unused)
+    const uint32_t pa = (uint32_t)a_rows * 32, pb = (uint32_t)N * 32;
     const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
     // cross terms (x part, y part) kept
     constexpr int NT = P == 2 ? 3 : 6;
@@ -355,7 +394,7 @@ __device__ inline void sync_after_epilogue() {
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_kernel(TcArgs a) {
   constexpr int kPlanes = 2 * P;
   constexpr int kRowBytes = 32 * kPlanes;
   extern __shared__ __align__(1024) char dyn[];
@@ -381,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sh.tmem;
+  const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
   uint32_t g = 0;           // ring position (thread 0)
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
@@ -401,17 +441,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
       outp[0] = tile;
       nk = 1;
     } else {
-      int lo = 0, hi = a.NA - 1;  // last row with row_start <= tile
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (a.row_start[mid] <= tile) lo = mid; else hi = mid - 1;
-      }
-      i = lo;
-      const int64_t t_in = tile - a.row_start[i];
-      const int j0 = (a.mode == 0 ? i + 1 : 0) + (int)(t_in * kG);
-      for (int q = 0; q < kG && j0 + q < a.NB; ++q) {
-        jj[q] = j0 + q;
-        outp[q] = (int64_t)i * a.ldk + j0 + q;
+      i = a.tiles[2 * tile];
+      const int j0 = a.tiles[2 * tile + 1];
+      // symmetric: only kets above the diagonal (the diagonal runs in FP64)
+      for (int j = (a.mode == 0 ? max(j0, i + 1) : j0); j < min(j0 + kG, a.NB); ++j) {
+        jj[nk] = j;
+        outp[nk] = (int64_t)i * a.ldk + j;
         ++nk;
       }
     }
@@ -423,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
     __syncthreads();
     if (tid < nk) {
       __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + tid * a.et_stride);
-      et[blk_off<kPlanes>(0, 0, 0, 16)] = __float2bfloat16_rn(1.f);
+      et[dyn_off<kPlanes>(0, 0, 0, 16)] = __float2bfloat16_rn(1.f);
     }
     sync_after_epilogue();
     const int32_t* da = a.a_dims + (int64_t)i * (n + 1);
@@ -431,17 +466,19 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
       const int ap = pad16(da[k]), ap1 = pad16(da[k + 1]);
       int q0 = 0;
       while (q0 < nk) {
-        // group kets while the stacked columns fit (<= 128)
+        // group kets while their stacked columns fit one MMA (<= 64); a ket
+        // wider than 64 forms a group of its own, split into 64-row slices
         int q1 = q0, ntot = 0;
         int nb[kG];
         while (q1 < nk) {
           const int w = pad16(a.b_dims[(int64_t)jj[q1] * (n + 1) + k + 1]);
-          if (q1 > q0 && ntot + w > 128) break;
+          if (q1 > q0 && ntot + w > kNMax) break;
           nb[q1] = ntot;
           ntot += w;
           ++q1;
+          if (ntot > kNMax) break;
         }
-        // ---- HS1 for each ket of the group
+        // ---- HS1 for each ket of the group: D1[(s,b'), a] over N slices of a
         for (int q = q0; q < q1; ++q) {
           const int32_t* db = a.b_dims + (int64_t)jj[q] * (n + 1);
           const int bp = pad16(db[k]), bp1 = pad16(db[k + 1]);
@@ -449,9 +486,56 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
           const char* bt = a.b_arena + a.b_bt[(int64_t)jj[q] * n + k];
           const char* et = scr + q * a.et_stride;
           for (int t = 0; t < nt; ++t) {
+            for (int h0 = 0; h0 < ap; h0 += kNMax) {
+              const int nh = min(kNMax, ap - h0);
+              if (tid == 0) {
+                const char* gA = bt + (int64_t)t * (bp / 16) * 128 * kRowBytes;
+                const char* gB = et + (int64_t)h0 * kRowBytes;
+                const int rt = tile_rows(rows, t);
+                if (!run_gemm<P>(sh, stage, gA, rt * kRowBytes, rt, gB, nh * kRowBytes, (int64_t)ap * kRowBytes,
+                                 bp / 16, mr, nh, g, pol_first, pol_last)) {
+                  sh.abort = 1;
+                  atomicExch(a.err, 1);
+                }
+              }
+              __syncthreads();
+              if (sh.abort) goto finish;
+              if (!wait_bar(&sh.done, done_phase & 1)) {
+                sh.abort = 1;
+                atomicExch(a.err, 1);
+              }
+              ++done_phase;
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              {
+                const int r = acc_row(mr);
+                const int R = t * 128 + r;
+                const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
+                __nv_bfloat16* Tb = reinterpret_cast<__nv_bfloat16*>(T_buf);
+                for (int c = 0; c < nh; c += 16) {
+                  float re[16], im[16];
+                  tmem_ld16(tmem + lane_base + c, re);
+                  tmem_ld16(tmem + lane_base + nh + c, im);
+                  if (r >= 0 && R < rows) {
+                    const int s = R / bp1, b1 = R % bp1;
+                    store_row16<P>(Tb, nb[q] + b1, s * ap + h0 + c, ntot, re, im, pol_last);
+                  }
+                }
+              }
+              sync_after_epilogue();
+              if (sh.abort) goto finish;
+            }
+          }
+        }
+        // ---- HS2 for the group: D2[a', (j,b')] over 64-row slices of T
+        {
+          const int mr = mrows_of(ap1);
+          const char* ah = a.a_arena + a.a_ah[(int64_t)i * n + k];
+          for (int h0 = 0; h0 < ntot; h0 += kNMax) {
+            const int nh = min(kNMax, ntot - h0);
             if (tid == 0) {
-              const char* gA = bt + (int64_t)t * (bp / 16) * mr * kRowBytes;
-              if (!run_gemm<P>(sh, stage, gA, mr * kRowBytes, et, ap * kRowBytes, bp / 16, mr, ap, g)) {
+              const char* gB = T_buf + (int64_t)h0 * kRowBytes;
+              if (!run_gemm<P>(sh, stage, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytes, (int64_t)ntot * kRowBytes,
+                               (2 * ap) / 16, mr, nh, g, pol_first, pol_last)) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
@@ -464,72 +548,37 @@ __global__ void __launch_bounds__(kThreads, 2) tc_overlap_kernel(TcArgs a) {
             }
             ++done_phase;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            {
-              const int r = acc_row(mr);
-              const int R = t * 128 + r;
-              const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
-              __nv_bfloat16* Tb = reinterpret_cast<__nv_bfloat16*>(T_buf);
-              for (int c = 0; c < ap; c += 16) {
+            const int r = acc_row(mr);
+            const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
+            for (int q = q0; q < q1; ++q) {
+              const int bp1 = pad16(a.b_dims[(int64_t)jj[q] * (n + 1) + k + 1]);
+              // columns of this slice that belong to ket q
+              const int c0 = max(nb[q], h0) - h0, c1 = min(nb[q] + bp1, h0 + nh) - h0;
+              if (c0 >= c1) continue;
+              if (k + 1 < n) {
+                __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
+                for (int c = c0; c < c1; c += 16) {
+                  float re[16], im[16];
+                  tmem_ld16(tmem + lane_base + c, re);
+                  tmem_ld16(tmem + lane_base + nh + c, im);
+                  if (r >= 0 && r < ap1) store_row16<P>(et, r, h0 + c - nb[q], ap1, re, im, pol_last);
+                }
+              } else if (nb[q] >= h0) {
+                // last site: 1 x 1 environments, z = E[0][0]
                 float re[16], im[16];
-                tmem_ld16(tmem + lane_base + c, re);
-                tmem_ld16(tmem + lane_base + ap + c, im);
-                if (r >= 0 && R < rows) {
-                  const int s = R / bp1, b1 = R % bp1;
-                  store_row16<P>(Tb, nb[q] + b1, s * ap + c, ntot, re, im);
+                tmem_ld16(tmem + lane_base + c0, re);
+                tmem_ld16(tmem + lane_base + nh + c0, im);
+                if (r == 0) {
+                  const double zr = re[0], zi = im[0];
+                  const double kv = zr * zr + zi * zi;
+                  a.K[outp[q]] = kv;
+                  if (a.mode == 0) a.K[(int64_t)jj[q] * a.ldk + i] = kv;
                 }
               }
             }
             sync_after_epilogue();
             if (sh.abort) goto finish;
           }
-        }
-        // ---- HS2 for the group
-        {
-          const int mr = mrows_of(ap1);
-          const char* ah = a.a_arena + a.a_ah[(int64_t)i * n + k];
-          if (tid == 0) {
-            if (!run_gemm<P>(sh, stage, ah, mr * kRowBytes, T_buf, ntot * kRowBytes, (2 * ap) / 16, mr, ntot, g)) {
-              sh.abort = 1;
-              atomicExch(a.err, 1);
-            }
-          }
-          __syncthreads();
-          if (sh.abort) goto finish;
-          if (!wait_bar(&sh.done, done_phase & 1)) {
-            sh.abort = 1;
-            atomicExch(a.err, 1);
-          }
-          ++done_phase;
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const int r = acc_row(mr);
-          const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
-          if (k + 1 < n) {
-            for (int q = q0; q < q1; ++q) {
-              const int bp1 = pad16(a.b_dims[(int64_t)jj[q] * (n + 1) + k + 1]);
-              __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
-              for (int c = 0; c < bp1; c += 16) {
-                float re[16], im[16];
-                tmem_ld16(tmem + lane_base + nb[q] + c, re);
-                tmem_ld16(tmem + lane_base + ntot + nb[q] + c, im);
-                if (r >= 0 && r < ap1) store_row16<P>(et, r, c, ap1, re, im);
-              }
-            }
-          } else {
-            // last site: 1 x 1 environments, z = E[0][0]
-            for (int q = q0; q < q1; ++q) {
-              float re[16], im[16];
-              tmem_ld16(tmem + lane_base + nb[q], re);
-              tmem_ld16(tmem + lane_base + ntot + nb[q], im);
-              if (r == 0) {
-                const double zr = re[0], zi = im[0];
-                const double kv = zr * zr + zi * zi;
-                a.K[outp[q]] = kv;
-                if (a.mode == 0) a.K[(int64_t)jj[q] * a.ldk + i] = kv;
-              }
-            }
-          }
-          sync_after_epilogue();
-          if (sh.abort) goto finish;
         }
         q0 = q1;
       }
@@ -612,9 +661,9 @@ qk_status ensure_tc_arena(qk_mps_batch* b, cudaStream_t st) {
       const int c0 = b->h_dims[s * (n + 1) + k], c1 = b->h_dims[s * (n + 1) + k + 1];
       const int p0 = pad16(c0), p1 = pad16(c1);
       bt[s * n + k] = off;
-      off += (int64_t)ntiles_of(2 * p1) * mrows_of(2 * p1) * p0 * 2 * kPlanes;
+      off += (int64_t)2 * p1 * p0 * 2 * kPlanes;
       ah[s * n + k] = off;
-      off += (int64_t)mrows_of(p1) * 2 * p0 * 2 * kPlanes;
+      off += (int64_t)p1 * 2 * p0 * 2 * kPlanes;
     }
   auto bail = [&](cudaError_t e, const char* w) {
     cudaFree(c.arena);
@@ -653,9 +702,12 @@ qk_status ensure_tc_arena(qk_mps_batch* b, cudaStream_t st) {
   return QK_OK;
 }
 
+// Enqueues the kernel on `st` without waiting for it; *err_out receives the
+// device error word for tc_finish (nullptr when nothing was launched).
 template <int P>
 qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, const int32_t* d_pairs,
-                    int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st) {
+                    int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st, int** err_out) {
+  *err_out = nullptr;
   constexpr int kPlanes = 2 * P;
   qk_status rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(A), st);
   if (rc != QK_OK) return rc;
@@ -666,20 +718,26 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   int dev = 0, sms = 0;
   QK_CUDA(cudaGetDevice(&dev));
   QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // tiles
-  std::vector<int64_t> row_start;
+  // tiles: (bra i, kets j0..j0+kG-1), in bands of kBand bras; within a band
+  // the ket groups are the outer loop, so the CTAs running at the same time
+  // share kets (and bras) in L2.  Symmetric: strict upper triangle only.
+  constexpr int kBand = 16;
+  std::vector<int32_t> tiles;
   int64_t n_tiles = 0;
   if (mode == 2) {
     n_tiles = P_pairs;
   } else {
-    row_start.resize(A->N + 1);
-    for (int64_t i = 0; i < A->N; ++i) {
-      row_start[i] = n_tiles;
-      // symmetric: strict upper triangle (the diagonal is contracted in FP64)
-      const int64_t cols = mode == 0 ? B->N - i - 1 : B->N;
-      n_tiles += (cols + kG - 1) / kG;
+    for (int64_t i0 = 0; i0 < A->N; i0 += kBand) {
+      const int64_t i1 = std::min<int64_t>(A->N, i0 + kBand);
+      const int64_t jstart = mode == 0 ? i0 + 1 : 0;
+      for (int64_t j0 = jstart; j0 < B->N; j0 += kG)
+        for (int64_t i = i0; i < i1; ++i) {
+          if (mode == 0 && std::min<int64_t>(j0 + kG, B->N) <= i + 1) continue;  // no ket above the diagonal
+          tiles.push_back((int32_t)i);
+          tiles.push_back((int32_t)j0);
+        }
     }
-    row_start[A->N] = n_tiles;
+    n_tiles = (int64_t)tiles.size() / 2;
   }
   if (n_tiles == 0) return QK_OK;
   // scratch: kG Et blocks (<= 128 x 128) + T (<= 128 rows x 256 K), bf16 planes
@@ -688,9 +746,9 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   const int64_t et_stride = (int64_t)cp * cp * 2 * kPlanes + 256;
   const int64_t t_bytes = (int64_t)128 * 2 * cp * 2 * kPlanes;
   const int64_t stride = ((kG * et_stride + t_bytes) + 1023) & ~int64_t(1023);
-  const int64_t ctas = std::min<int64_t>((int64_t)2 * sms, n_tiles);
+  const int64_t ctas = std::min<int64_t>((int64_t)Stage<P>::ctas_per_sm * sms, n_tiles);
   char* scratch = nullptr;
-  int64_t* d_rs = nullptr;
+  int32_t* d_tiles = nullptr;
   unsigned long long* queue = nullptr;
   int* err = nullptr;
   QK_CUDA(cudaMallocAsync(&scratch, stride * ctas, st));
@@ -698,9 +756,9 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   QK_CUDA(cudaMallocAsync(&err, sizeof(int), st));
   QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st));
   QK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  if (!row_start.empty()) {
-    QK_CUDA(cudaMallocAsync(&d_rs, sizeof(int64_t) * row_start.size(), st));
-    QK_CUDA(cudaMemcpyAsync(d_rs, row_start.data(), sizeof(int64_t) * row_start.size(), cudaMemcpyHostToDevice, st));
+  if (!tiles.empty()) {
+    QK_CUDA(cudaMallocAsync(&d_tiles, sizeof(int32_t) * tiles.size(), st));
+    QK_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int32_t) * tiles.size(), cudaMemcpyHostToDevice, st));
   }
   TcArgs a;
   a.a_dims = A->d_dims;
@@ -712,7 +770,7 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.n = A->n;
   a.mode = mode;
   a.n_tiles = n_tiles;
-  a.row_start = d_rs;
+  a.tiles = d_tiles;
   a.NA = (int)A->N;
   a.NB = (int)B->N;
   a.pairs = d_pairs;
@@ -723,28 +781,41 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.et_stride = et_stride;
   a.queue = queue;
   a.err = err;
-  const int smem = kStages * 2 * kStageBytes;
+  const int smem = kStages * Stage<P>::bytes;
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   timer_mark(false, st);
   tc_overlap_kernel<P><<<(int)ctas, kThreads, smem, st>>>(a);
   timer_mark(true, st);
   cudaError_t e = cudaGetLastError();
-  int herr = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(scratch, st);
   cudaFreeAsync(queue, st);
+  if (d_tiles) cudaFreeAsync(d_tiles, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(err, st);
+    return cuda_fail(e, "tc_overlap_kernel");
+  }
+  *err_out = err;  // read (and freed) by tc_finish after the stream is synchronised
+  return QK_OK;
+}
+
+// Reads the kernel's error word once the stream has been synchronised.
+qk_status tc_finish(int* err, cudaStream_t st) {
+  if (!err) return QK_OK;
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(err, st);
-  if (d_rs) cudaFreeAsync(d_rs, st);
   if (e != cudaSuccess) return cuda_fail(e, "tc_overlap_kernel");
   if (herr) return fail(QK_ERR_TIMEOUT, "tc_overlap_kernel: a bounded wait ran out");
   return QK_OK;
 }
 
 qk_status launch_tc_parts(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode,
-                          const int32_t* d_pairs, int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st) {
-  return parts == 3 ? launch_tc<3>(A, B, mode, d_pairs, P_pairs, dK, ldk, st)
-                    : launch_tc<2>(A, B, mode, d_pairs, P_pairs, dK, ldk, st);
+                          const int32_t* d_pairs, int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st,
+                          int** err_out) {
+  return parts == 3 ? launch_tc<3>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out)
+                    : launch_tc<2>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out);
 }
 
 }  // namespace
@@ -765,40 +836,42 @@ qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, do
                      double refine_floor, cudaStream_t st, int64_t* n_refined) {
   const bool sym = (A == B);
   int64_t n_diag = 0;
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_ready = nullptr, ev_diag = nullptr;
-  int32_t* dpairs = nullptr;
-  qk_status rc = QK_OK;
-  if (sym) {
+  int* tc_err = nullptr;
+  // the tensor-core kernel first: it takes every SM's registers, and the FP64
+  // diagonal below only fills SMs as the tensor-core kernel drains
+  qk_status rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st, &tc_err);
+  if (rc == QK_OK && sym) {
     // The diagonal (K_ii ~ 1, above the FP64 ceiling by construction) runs in
-    // FP64 on a second stream, one CTA per SM, while the tensor-core kernel
-    // contracts the strict upper triangle: the FP64 pipe and the tensor pipe
-    // work at the same time.
+    // FP64 on a second stream; its CTAs take SMs as the tensor-core kernel
+    // releases them.
     n_diag = A->N;
     std::vector<int32_t> hp(2 * n_diag);
     for (int64_t i = 0; i < n_diag; ++i) hp[2 * i] = hp[2 * i + 1] = (int32_t)i;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_diag = nullptr;
+    int32_t* dpairs = nullptr;
     QK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
     QK_CUDA(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
     QK_CUDA(cudaEventCreateWithFlags(&ev_diag, cudaEventDisableTiming));
+    // ev_ready after the tensor-core launch: the side stream's work is ordered
+    // after everything enqueued before this call, and runs beside the kernel
     QK_CUDA(cudaEventRecord(ev_ready, st));
     QK_CUDA(cudaStreamWaitEvent(side, ev_ready, 0));
     QK_CUDA(cudaMallocAsync(&dpairs, sizeof(int32_t) * 2 * n_diag, side));
     QK_CUDA(cudaMemcpyAsync(dpairs, hp.data(), sizeof(int32_t) * 2 * n_diag, cudaMemcpyHostToDevice, side));
     timer_set_phase(1);
-    rc = overlap_fp64(A, A, dpairs, n_diag, dK, ldk, false, side, 1);
+    rc = overlap_fp64(A, A, dpairs, n_diag, dK, ldk, false, side);
     timer_set_phase(0);
     cudaFreeAsync(dpairs, side);
     cudaEventRecord(ev_diag, side);
-    // hp may go: a pageable host-to-device copy has staged it on return
-  }
-  if (rc == QK_OK) rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st);
-  if (sym) {
     cudaStreamWaitEvent(st, ev_diag, 0);
     cudaStreamSynchronize(st);
     cudaEventDestroy(ev_ready);
     cudaEventDestroy(ev_diag);
     cudaStreamDestroy(side);
   }
+  qk_status rc2 = tc_finish(tc_err, st);
+  if (rc == QK_OK) rc = rc2;
   if (rc != QK_OK) return rc;
   // FP64 re-evaluation of the off-diagonal entries below the floor and above
   // the ceiling
@@ -831,7 +904,10 @@ qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, do
 
 qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* d_pairs,
                       int64_t P, double* dK, cudaStream_t st) {
-  qk_status rc = launch_tc_parts(parts, A, B, 2, d_pairs, P, dK, 0, st);
+  int* tc_err = nullptr;
+  qk_status rc = launch_tc_parts(parts, A, B, 2, d_pairs, P, dK, 0, st, &tc_err);
+  qk_status rc2 = tc_finish(tc_err, st);
+  if (rc == QK_OK) rc = rc2;
   if (rc != QK_OK) return rc;
   int32_t* sel = nullptr;
   int64_t* pos = nullptr;
