@@ -28,8 +28,9 @@ def nvcc() -> str:
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    extra = os.environ.get("QK_NVCC_FLAGS", "").split()  # e.g. -DQK_TC_CTAS=2 for tuning runs
     cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
-           "--expt-relaxed-constexpr", *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+           "--expt-relaxed-constexpr", *ARCH, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "cu")

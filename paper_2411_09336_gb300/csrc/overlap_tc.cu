@@ -19,8 +19,8 @@
 // all accumulated in FP32 in TMEM.  The static (per-state) operands Bt/Ah are packed once
 // per batch (tc_pack_kernel); E and T live in a per-CTA global scratch that
 // the epilogue writes (tcgen05.ld -> split -> st.global) and the next GEMM
-// streams back with 1-D bulk copies.  One elected thread keeps a 2-stage
-// mbarrier ring of bulk copies ahead of its MMAs; every wait is bounded in
+// streams back with 1-D bulk copies.  One elected thread keeps a byte ring
+// of up to eight chunks of bulk copies in flight ahead of its MMAs; every wait is bounded in
 // time and reports QK_ERR_TIMEOUT instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -40,15 +40,24 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kG = 4;            // kets per tile
-constexpr int kStages = 2;
-constexpr int kNMax = 64;       // N of one MMA: re and im accumulators fill 2 x 64 TMEM columns
-constexpr int kTmemCols = 128;  // four CTAs share an SM's 512 columns
+// Residency: QK_TC_CTAS CTAs per SM share its 512 TMEM columns and shared
+// memory; the N of one MMA (kNMax) is sized so re and im accumulators fit.
+#ifndef QK_TC_CTAS
+#define QK_TC_CTAS 4
+#endif
+constexpr int kCtas = QK_TC_CTAS;
+constexpr int kTmemCols = kCtas <= 2 ? 256 : 128;
+constexpr int kNMax = kTmemCols / 2;  // N of one MMA
 template <int P>
 struct Stage {
   static constexpr int A = 128 * 32 * 2 * P;    // 128 rows of one 16-wide K chunk, all planes
-  static constexpr int B = kNMax * 32 * 2 * P;  // up to 64 rows
+  static constexpr int B = kNMax * 32 * 2 * P;  // up to kNMax rows
+  static constexpr int ctas_per_sm = P == 2 ? kCtas : (kCtas < 3 ? kCtas : 3);
+  // ring: what the SM's shared memory allows per CTA, at least two chunks
+  static constexpr int ring = ((220 * 1024 / ctas_per_sm) / 1024) * 1024 > 2 * (A + B)
+                                  ? ((220 * 1024 / ctas_per_sm) / 1024) * 1024
+                                  : 2 * (A + B);
   static constexpr int bytes = A + B;
-  static constexpr int ctas_per_sm = P == 2 ? 4 : 3;
 };
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 
@@ -311,50 +320,83 @@ struct TcArgs {
   int* err;
 };
 
+constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
+
 struct __align__(8) TcShared {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t full[kSlots];
+  uint64_t empty[kSlots];
   uint64_t done;
   uint32_t tmem;
   int abort;
   int64_t tile;
 };
 
-// Streams `nchunks` K-chunks of (A block, B block) through the ring and issues
-// the 4 x (split products) MMAs per chunk into TMEM columns [0, N) (re) and
-// [N, 2N) (im).  Called by thread 0 only.  g is the running chunk counter.
+// Byte ring of operand chunks in shared memory (thread 0's bookkeeping).
+// Chunk g (a running count over all GEMMs of the CTA) uses mbarrier slot
+// g % kSlots; its A and B blocks sit contiguously at off[slot], len[slot]
+// bytes including any padding skipped at the ring's end.  Chunks are
+// reclaimed in order once the MMAs that read them have completed.
+struct Ring {
+  uint32_t produced = 0, released = 0;
+  uint32_t head = 0, tail = 0;  // bytes ever produced / reclaimed
+  uint32_t off[kSlots], len[kSlots];
+};
+
+__device__ inline bool ring_release(TcShared& sh, Ring& r) {
+  const uint32_t j = r.released, slot = j % kSlots;
+  if (!wait_bar(&sh.empty[slot], (j / kSlots) & 1)) return false;
+  r.tail += r.len[slot];
+  ++r.released;
+  return true;
+}
+
+// Streams `nchunks` K-chunks of (A block, B block) through the ring, keeping
+// as many bulk copies in flight as the ring holds, and issues the
+// 4 x (split products) MMAs per chunk into TMEM columns [0, N) (re) and
+// [N, 2N) (im).  Called by thread 0 only.
 template <int P>
-__device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_bytes, int a_rows, const char* gB,
-                         uint32_t b_bytes, int64_t b_stride, int nchunks, int M, int N, uint32_t& g, uint64_t pol_a,
-                         uint64_t pol_b) {
-  constexpr int kStageA = Stage<P>::A, kStageBytes = Stage<P>::bytes;
+__device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg, const char* gA,
+                         uint32_t a_bytes, int a_rows, const char* gB, uint32_t b_bytes, int64_t b_stride,
+                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b) {
   const uint32_t id_pos = make_idesc(M, N, 0), id_neg = make_idesc(M, N, 1);
   const uint32_t t_re = sh.tmem, t_im = sh.tmem + N;
-  auto produce = [&](int c, uint32_t gi) -> bool {
-    const int slot = gi % kStages;
-    if (gi >= (uint32_t)kStages && !wait_bar(&sh.empty[slot], ((gi / kStages) - 1) & 1)) return false;
-    char* sA = stage + slot * kStageBytes;
-    char* sB = sA + kStageA;
-    expect_tx(&sh.full[slot], a_bytes + b_bytes);
-    bulk_load(sA, gA + (int64_t)c * a_bytes, a_bytes, &sh.full[slot], pol_a);
-    bulk_load(sB, gB + (int64_t)c * b_stride, b_bytes, &sh.full[slot], pol_b);
+  // The MMA reads M rows of every A plane; the planes hold a_rows <= M rows,
+  // so the last plane's read runs (M - a_rows) rows past the A block.  The
+  // ring reserves that span (the extra rows feed unused accumulator rows).
+  const uint32_t a_span = (uint32_t)(2 * P - 1) * a_rows * 32 + (uint32_t)M * 32;
+  const uint32_t g0 = rg.produced, size = a_span + b_bytes;
+  int p = 0;  // chunks of this GEMM issued
+  // issue loads while space and slots allow, reclaiming only chunks < limit
+  auto top_up = [&](uint32_t limit) -> bool {
+    while (p < nchunks) {
+      const uint32_t gi = g0 + p;
+      const uint32_t pos = rg.head % ring_bytes;
+      const uint32_t pad = pos + size > ring_bytes ? ring_bytes - pos : 0;
+      while ((rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) &&
+             rg.released < limit)
+        if (!ring_release(sh, rg)) return false;
+      if (rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) break;
+      const uint32_t slot = gi % kSlots, off = (pos + pad) % ring_bytes;
+      rg.off[slot] = off;
+      rg.len[slot] = pad + size;
+      rg.head += pad + size;
+      expect_tx(&sh.full[slot], a_bytes + b_bytes);
+      bulk_load(ring + off, gA + (int64_t)p * a_bytes, a_bytes, &sh.full[slot], pol_a);
+      bulk_load(ring + off + a_span, gB + (int64_t)p * b_stride, b_bytes, &sh.full[slot], pol_b);
+      ++p;
+    }
     return true;
   };
-  const uint32_t g0 = g;
-  const int look = kStages - 1;
-  for (int c = 0; c < look && c < nchunks; ++c)
-    if (!produce(c, g0 + c)) return false;
+  if (!top_up(g0)) return false;
   for (int c = 0; c < nchunks; ++c) {
-    const uint32_t gi = g0 + c;
-    const int slot = gi % kStages;
-    if (!wait_bar(&sh.full[slot], (gi / kStages) & 1)) return false;
+    const uint32_t gi = g0 + c, slot = gi % kSlots;
+    if (p <= c && !top_up(gi)) return false;  // reclaims everything before chunk c
+    if (!wait_bar(&sh.full[slot], (gi / kSlots) & 1)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const char* sA = stage + slot * kStageBytes;
-    const char* sB = sA + kStageA;
     // bytes per plane: A is stored with a_rows rows (rows of the M tile past
     // a_rows read other data and only feed accumulator rows that are unused)
     const uint32_t pa = (uint32_t)a_rows * 32, pb = (uint32_t)N * 32;
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    const uint32_t a0 = smem_u32(ring + rg.off[slot]), b0 = a0 + a_span;
     // cross terms (x part, y part) kept
     constexpr int NT = P == 2 ? 3 : 6;
     const int xs[6] = {0, 0, 1, 0, 1, 2};
@@ -371,10 +413,11 @@ __device__ bool run_gemm(TcShared& sh, char* stage, const char* gA, uint32_t a_b
       mma(t_im, ai, br, id_pos, 1);
     }
     commit(&sh.empty[slot]);
-    if (c + look < nchunks && !produce(c + look, g0 + c + look)) return false;
+    // refill behind this chunk: chunks before it may be reclaimed
+    if (!top_up(gi)) return false;
   }
   commit(&sh.done);
-  g = g0 + nchunks;
+  rg.produced = g0 + nchunks;
   return true;
 }
 
@@ -408,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kSlots; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.empty[s])));
     }
@@ -421,7 +464,8 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sh.tmem;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
-  uint32_t g = 0;           // ring position (thread 0)
+  Ring rg;                  // operand ring (thread 0)
+  const uint32_t ring_bytes = Stage<P>::ring;
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
   char* T_buf = scr + (int64_t)kG * a.et_stride;
@@ -492,8 +536,8 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                 const char* gA = bt + (int64_t)t * (bp / 16) * 128 * kRowBytes;
                 const char* gB = et + (int64_t)h0 * kRowBytes;
                 const int rt = tile_rows(rows, t);
-                if (!run_gemm<P>(sh, stage, gA, rt * kRowBytes, rt, gB, nh * kRowBytes, (int64_t)ap * kRowBytes,
-                                 bp / 16, mr, nh, g, pol_first, pol_last)) {
+                if (!run_gemm<P>(sh, stage, ring_bytes, rg, gA, rt * kRowBytes, rt, gB, nh * kRowBytes,
+                                 (int64_t)ap * kRowBytes, bp / 16, mr, nh, pol_first, pol_last)) {
                   sh.abort = 1;
                   atomicExch(a.err, 1);
                 }
@@ -534,8 +578,8 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
             const int nh = min(kNMax, ntot - h0);
             if (tid == 0) {
               const char* gB = T_buf + (int64_t)h0 * kRowBytes;
-              if (!run_gemm<P>(sh, stage, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytes, (int64_t)ntot * kRowBytes,
-                               (2 * ap) / 16, mr, nh, g, pol_first, pol_last)) {
+              if (!run_gemm<P>(sh, stage, ring_bytes, rg, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytes,
+                               (int64_t)ntot * kRowBytes, (2 * ap) / 16, mr, nh, pol_first, pol_last)) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
@@ -781,7 +825,7 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.et_stride = et_stride;
   a.queue = queue;
   a.err = err;
-  const int smem = kStages * Stage<P>::bytes;
+  const int smem = Stage<P>::ring;
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   timer_mark(false, st);
