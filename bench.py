@@ -39,6 +39,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gram entries/s (n=165, chi=128), split-precision vs FP64 path on 1 GB300 at |dK|<=1e-5"
 
+# DRAM bytes (read + write) per off-diagonal pair of tc_overlap_kernel<2> at
+# the n=165, d=6, chi_max=128 circuit, from one ncu capture of a 192-state
+# symmetric Gram (18,336 pairs, 568.2 GB in one launch).  The roofline's
+# `traffic` scales it to the pairs of one launch; it holds only for that
+# kernel version and the split depth P=2.
+TC_DRAM_BYTES_PER_PAIR = 568.189336e9 / 18336
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -62,17 +69,43 @@ def dist_env():
     return rank, world, local
 
 
+def rank_rows(X: np.ndarray, rank: int, distinct: int) -> np.ndarray:
+    """Training rows of one rank: disjoint consecutive blocks, so every rank
+    builds and contracts its own independent batch (weak scaling)."""
+    rows = X[rank * distinct:(rank + 1) * distinct]
+    if len(rows) != distinct:
+        raise ValueError(f"rank {rank}: only {len(rows)} of {distinct} training rows left")
+    return rows
+
+
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The step time every rank reports: the slowest rank's."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------- helpers
-def gram_flops(dims: np.ndarray) -> float:
-    """Algorithmic real FLOPs of the symmetric Gram (pairs i <= j): per pair
-    and site, T_s = E B[s] then E' = sum_s A[s]^H T_s, i.e.
-    2 (chi^a_k chi^b_k chi^b_k+1 + chi^a_k+1 chi^a_k chi^b_k+1) complex MACs,
-    8 real FLOPs each."""
+def gram_flops(dims: np.ndarray, diagonal: bool = False) -> float:
+    """Algorithmic real FLOPs of the pairs (bra i, ket j), i < j (and i = j
+    when `diagonal`): per pair and site, T_s = E B[s] then
+    E' = sum_s A[s]^H T_s, i.e. 2 (chi^a_k chi^b_k chi^b_k+1 +
+    chi^a_k+1 chi^a_k chi^b_k+1) complex MACs, 8 real FLOPs each.  The count
+    is not symmetric in (i, j), so it is summed in order with prefix sums."""
     c = dims.astype(np.float64)
     c0, c1 = c[:, :-1], c[:, 1:]
-    full = np.sum(c0.sum(0) * (c0 * c1).sum(0)) + np.sum((c1 * c0).sum(0) * c1.sum(0))
-    diag = np.sum(c0 * c0 * c1 + c1 * c0 * c1)
-    return 16.0 * (full + diag) / 2.0
+    bra1, ket1 = c0, c0 * c1          # chi^a_k      * (chi^b_k chi^b_k+1)
+    bra2, ket2 = c1 * c0, c1          # chi^a_k+1 chi^a_k * chi^b_k+1
+    pre1 = np.cumsum(bra1, axis=0) - bra1  # sum over i < j
+    pre2 = np.cumsum(bra2, axis=0) - bra2
+    total = np.sum(ket1 * pre1) + np.sum(ket2 * pre2)
+    if diagonal:
+        total += np.sum(bra1 * ket1 + bra2 * ket2)
+    return 16.0 * total
 
 
 class ClockSampler:
@@ -190,8 +223,7 @@ def run_ours(a):
     import workloads
 
     w = workloads.c165()
-    rows = w.X_train[rank * a.distinct:(rank + 1) * a.distinct]
-    assert len(rows) == a.distinct, "not enough training rows for this rank"
+    rows = rank_rows(w.X_train, rank, a.distinct)
     stream = torch.cuda.current_stream()
 
     # ---- setup: FP64 builder, then rotated copies
@@ -234,11 +266,7 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     entries = N * (N + 1) // 2
     value = entries * world * a.steps / (ms / 1000.0)
 
@@ -273,6 +301,15 @@ def run_ours(a):
         e2e = {"value": entries * world / dt, "unit": "entries/s", "h2d_bytes_per_step": int(nb),
                "d2h_bytes_per_step": int(N * N * 8)}
 
+    # kernels of one split qk_gram on a symmetric batch: the tensor-core sweep,
+    # the self-overlaps, the refinement selection, and, when entries were
+    # selected, the FP64 sweep over them and their scatter into K
+    if a.prec == "fp64":
+        launches = a.steps
+    else:
+        launches = sum(3 + (2 if r > N else 0) for r in nrefs)
+    pairs = N * (N - 1) // 2
+    traffic = TC_DRAM_BYTES_PER_PAIR * pairs if a.prec == "split" else None
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     kavg = float(np.mean(kern_ms)) if kern_ms else float("nan")
@@ -290,14 +327,17 @@ def run_ours(a):
                    "prec": a.prec, "l2": "inputs larger than L2 (packed states GBs)",
                    "mean_chi": float(dims.mean()), "max_chi": int(dims.max())},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "tc_overlap_kernel", "peak_source": f"bf16_tflops_sustained ({src})",
                      "algorithmic_tflop_per_launch": flops / 1e12,
                      "kernel_ms_per_launch": kavg, "refine_ms_per_step": float(np.mean(refine_ms)),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 192-state "
+                                       "capture, per pair, times the launch's pairs",
+                     "dram_tb_per_s": (traffic / (kavg / 1000.0) / 1e12) if traffic else None,
                      "note": "algorithmic complex-MAC FLOPs; the bf16x2 split issues 3 bf16 products per "
                              "real product, so frac <= 1/3 at full tensor-pipe use"},
         "clocks": clocks,
-        "gpu_launches": 4 * a.steps,
+        "gpu_launches": launches,
         "e2e": e2e,
         "fp64_path": fp64,
         "builder": {"states": base.N, "seconds": round(build_s, 1), "states_per_s": base.N / build_s},

@@ -178,7 +178,15 @@ qk_status qk_last_profile(double* overlap_ms, double* refine_ms,
  *   refine_floor  split path only: entries with K < refine_floor are
  *            contracted again in FP64 (0 disables); entries with
  *            K > QK_SPLIT_REFINE_ABOVE always are.
- *   n_refined     optional host out: entries re-evaluated in FP64.
+ *   n_refined     optional host out: entries not taken from the split
+ *            product -- those re-evaluated in FP64 and, when B == A, the
+ *            N self-overlaps.
+ * Split path, B == A: the self-overlaps K_ii come from the recursion
+ * E_k = I + F_k, F_k+1 = G_k + sum_s A_k[s]^H F_k A_k[s] with the site's
+ * isometry defect G_k = sum_s A_k[s]^H A_k[s] - I formed in double-float
+ * arithmetic (exact for a left-canonical state, which keeps E = I; within
+ * ~1e-10 of the FP64 sweep); states whose defect exceeds 1e-4 (not
+ * left-canonical) take the FP64 sweep.
  * Synchronises.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT.
  * ---------------------------------------------------------------------- */
 qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, double* K,

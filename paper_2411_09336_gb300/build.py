@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["abi.cu", "schedule.cpp", "builder.cu", "overlap_fp64.cu", "overlap_tc.cu", "surrogate.cu", "batch_ops.cu"]
+SOURCES = ["abi.cu", "schedule.cpp", "builder.cu", "overlap_fp64.cu", "overlap_tc.cu", "surrogate.cu", "batch_ops.cu", "diag.cu"]
 
 
 def nvcc() -> str:

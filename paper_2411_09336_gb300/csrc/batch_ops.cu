@@ -11,31 +11,48 @@
 namespace qk {
 
 // ---- per-call timing (CUDA events on the call's stream) -------------------
-static thread_local cudaEvent_t g_ev[4] = {nullptr, nullptr, nullptr, nullptr};
-static thread_local bool g_rec[4] = {false, false, false, false};
+// Each phase keeps up to kSpans (start, end) event pairs; a phase's time is
+// the sum of its spans, so several launches of one phase add up.
+constexpr int kSpans = 8;
+static thread_local cudaEvent_t g_ev[2][kSpans][2] = {};
+static thread_local int g_nspan[2] = {0, 0};
+static thread_local bool g_open[2] = {false, false};
 static thread_local int g_phase = 0;  // 0: main sweep, 1: refinement
 static thread_local double g_prof[3] = {0.0, 0.0, 0.0};
 
 void timer_begin_call() {
-  for (int i = 0; i < 4; ++i) {
-    if (!g_ev[i]) cudaEventCreate(&g_ev[i]);
-    g_rec[i] = false;
+  for (int p = 0; p < 2; ++p) {
+    g_nspan[p] = 0;
+    g_open[p] = false;
   }
   g_phase = 0;
   g_prof[0] = g_prof[1] = g_prof[2] = 0.0;
 }
 void timer_set_phase(int phase) { g_phase = phase; }
 void timer_mark(bool end, cudaStream_t st) {
-  const int i = 2 * g_phase + (end ? 1 : 0);
-  if (g_ev[i]) {
-    cudaEventRecord(g_ev[i], st);
-    g_rec[i] = true;
+  const int p = g_phase;
+  if (!end) {
+    if (g_nspan[p] >= kSpans) return;  // further spans are not timed
+    int i = g_nspan[p];
+    for (int k = 0; k < 2; ++k)
+      if (!g_ev[p][i][k]) cudaEventCreate(&g_ev[p][i][k]);
+    cudaEventRecord(g_ev[p][i][0], st);
+    g_open[p] = true;
+  } else if (g_open[p]) {
+    cudaEventRecord(g_ev[p][g_nspan[p]][1], st);
+    g_open[p] = false;
+    ++g_nspan[p];
   }
 }
 void timer_end_call(double total_ms) {
-  float ms = 0.f;
-  g_prof[0] = (g_rec[0] && g_rec[1] && cudaEventElapsedTime(&ms, g_ev[0], g_ev[1]) == cudaSuccess) ? ms : 0.0;
-  g_prof[1] = (g_rec[2] && g_rec[3] && cudaEventElapsedTime(&ms, g_ev[2], g_ev[3]) == cudaSuccess) ? ms : 0.0;
+  for (int p = 0; p < 2; ++p) {
+    double sum = 0.0;
+    for (int i = 0; i < g_nspan[p]; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, g_ev[p][i][0], g_ev[p][i][1]) == cudaSuccess) sum += ms;
+    }
+    g_prof[p] = sum;
+  }
   g_prof[2] = total_ms;
   cudaGetLastError();
 }

@@ -881,38 +881,15 @@ qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, do
   const bool sym = (A == B);
   int64_t n_diag = 0;
   int* tc_err = nullptr;
-  // the tensor-core kernel first: it takes every SM's registers, and the FP64
-  // diagonal below only fills SMs as the tensor-core kernel drains
   qk_status rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st, &tc_err);
   if (rc == QK_OK && sym) {
-    // The diagonal (K_ii ~ 1, above the FP64 ceiling by construction) runs in
-    // FP64 on a second stream; its CTAs take SMs as the tensor-core kernel
-    // releases them.
+    // The diagonal (K_ii ~ 1, above the refinement ceiling by construction)
+    // comes from the isometry-defect recursion, which needs no FP64 sweep for
+    // left-canonical states; it runs after the strict upper triangle.
     n_diag = A->N;
-    std::vector<int32_t> hp(2 * n_diag);
-    for (int64_t i = 0; i < n_diag; ++i) hp[2 * i] = hp[2 * i + 1] = (int32_t)i;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_ready = nullptr, ev_diag = nullptr;
-    int32_t* dpairs = nullptr;
-    QK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    QK_CUDA(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
-    QK_CUDA(cudaEventCreateWithFlags(&ev_diag, cudaEventDisableTiming));
-    // ev_ready after the tensor-core launch: the side stream's work is ordered
-    // after everything enqueued before this call, and runs beside the kernel
-    QK_CUDA(cudaEventRecord(ev_ready, st));
-    QK_CUDA(cudaStreamWaitEvent(side, ev_ready, 0));
-    QK_CUDA(cudaMallocAsync(&dpairs, sizeof(int32_t) * 2 * n_diag, side));
-    QK_CUDA(cudaMemcpyAsync(dpairs, hp.data(), sizeof(int32_t) * 2 * n_diag, cudaMemcpyHostToDevice, side));
     timer_set_phase(1);
-    rc = overlap_fp64(A, A, dpairs, n_diag, dK, ldk, false, side);
+    rc = diag_self_overlaps(A, dK, ldk, st, nullptr);
     timer_set_phase(0);
-    cudaFreeAsync(dpairs, side);
-    cudaEventRecord(ev_diag, side);
-    cudaStreamWaitEvent(st, ev_diag, 0);
-    cudaStreamSynchronize(st);
-    cudaEventDestroy(ev_ready);
-    cudaEventDestroy(ev_diag);
-    cudaStreamDestroy(side);
   }
   qk_status rc2 = tc_finish(tc_err, st);
   if (rc == QK_OK) rc = rc2;

@@ -78,4 +78,9 @@ void timer_end_call(double total_ms);
 size_t elem_bytes(qk_store s);
 void free_batch_memory(qk_mps_batch* b);
 void free_tc_cache(qk_mps_batch* b);
+// K[i*ldk + i] = |<psi_i|psi_i>|^2 for all states of a batch: the
+// isometry-defect recursion for left-canonical complex64 states, the FP64
+// sweep for the rest (their count in *n_fp64).  Synchronises the stream.
+qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st,
+                             int64_t* n_fp64);
 }  // namespace qk

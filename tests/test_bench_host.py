@@ -1,0 +1,74 @@
+"""Host-side logic of bench.py: the algorithmic FLOP count against brute
+force, and the multi-rank sharding / max-over-ranks timing on two gloo
+ranks (CPU)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_gram_flops_brute_force():
+    rng = np.random.default_rng(0)
+    N, n = 7, 9
+    dims = np.ones((N, n + 1), dtype=np.int64)
+    dims[:, 1:-1] = rng.integers(1, 40, size=(N, n - 1))
+    strict, diag = 0.0, 0.0
+    for i in range(N):
+        for j in range(i, N):
+            a, b = dims[i], dims[j]   # bra i, ket j
+            f = sum(16.0 * (a[k] * b[k] * b[k + 1] + a[k + 1] * a[k] * b[k + 1]) for k in range(n))
+            if i == j:
+                diag += f
+            else:
+                strict += f
+    assert bench.gram_flops(dims) == pytest.approx(strict, rel=1e-12)
+    assert bench.gram_flops(dims, diagonal=True) == pytest.approx(strict + diag, rel=1e-12)
+
+
+def test_rank_rows_disjoint_and_checked():
+    X = np.arange(40 * 3, dtype=float).reshape(40, 3)
+    blocks = [bench.rank_rows(X, r, 8) for r in range(5)]
+    flat = np.concatenate([b[:, 0] for b in blocks])
+    assert len(np.unique(flat)) == 40
+    with pytest.raises(ValueError):
+        bench.rank_rows(X, 5, 8)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    X = np.arange(100 * 2, dtype=float).reshape(100, 2)
+    rows = bench.rank_rows(X, rank, 10)
+    ms = bench.max_over_ranks([3.5, 7.25][rank], world, device="cpu")
+    out.put((rank, ms, rows[:, 0].tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res.sort()
+    assert res[0][1] == res[1][1] == 7.25
+    assert set(res[0][2]).isdisjoint(res[1][2])

@@ -91,10 +91,13 @@ def test_c50_split_vs_fp64_and_refine(qk):
     Ks_n, K64_n = Ks.cpu().numpy(), K64.cpu().numpy()
     iu = np.triu_indices(40)
     ceil = qk.QK_SPLIT_REFINE_ABOVE
-    # entries above the ceiling (the diagonal at least) come from FP64
+    # entries above the ceiling (the diagonal at least) do not come from the
+    # split product: off the diagonal they are the FP64 sweep's, bit for bit;
+    # the self-overlaps come from the isometry-defect recursion
     assert nref == int(np.sum(Ks_n[iu] > ceil)) >= 40
-    hi = Ks_n > ceil
+    hi = (Ks_n > ceil) & ~np.eye(40, dtype=bool)
     assert np.array_equal(Ks_n[hi], K64_n[hi])
+    assert np.max(np.abs(np.diag(Ks_n) - np.diag(K64_n))) <= 1e-9
     check(Ks_n, K64_n)
     # refinement: entries below the floor are re-evaluated in FP64 as well
     floor = float(np.median(K64_n))
@@ -116,3 +119,37 @@ def test_c165_sampled_full_size(qk):
     for prec, rel in (("split", 5e-3), ("split_bf16x3", 1e-3)):
         Ks, _ = qk.qk_gram(A, prec=prec)
         check(Ks.cpu().numpy(), K64.cpu().numpy(), rel=rel)
+
+
+def test_self_overlaps_defect_recursion_and_fallback(qk):
+    """The split path's diagonal: left-canonical states (also with a small
+    norm defect on the last site) through the isometry-defect recursion,
+    within 1e-9 of the FP64 sweep; states that are not left-canonical (a
+    norm defect above the recursion's limit, random sites) fall back to the
+    FP64 sweep, bit for bit."""
+    base = ragged_states(8, 14, seed=21, chis=(8, 16, 32, 64))
+    rng = np.random.default_rng(5)
+    states, exact = [], []
+    for s, st in enumerate(base):
+        st = [a.copy() for a in st]
+        if s % 4 == 1:
+            st[-1] = st[-1] * (1 + 1e-6)        # defect 2e-6: recursion
+        elif s % 4 == 2:
+            st[-1] = st[-1] * 1.01               # defect 2e-2: FP64
+            exact.append(s)
+        elif s % 4 == 3:                          # not canonical: FP64
+            chis = [1] + [min(2 ** min(k + 1, 14 - k - 1), 8) for k in range(13)] + [1]
+            st = [(rng.standard_normal((chis[k], 2, chis[k + 1]))
+                   + 1j * rng.standard_normal((chis[k], 2, chis[k + 1]))) / (2 * np.sqrt(chis[k]))
+                  for k in range(14)]
+            exact.append(s)
+        states.append(st)
+    A = qk.qk_mps_import(states, store="c64")
+    K64, _ = qk.qk_gram(A, prec="fp64")
+    d64 = np.diag(K64.cpu().numpy())
+    for prec in PRECS:
+        Ks, nref = qk.qk_gram(A, prec=prec)
+        d = np.diag(Ks.cpu().numpy())
+        assert np.array_equal(d[exact], d64[exact])
+        assert np.max(np.abs(d - d64) / np.maximum(d64, 1.0)) <= 1e-9
+        assert nref >= len(states)
