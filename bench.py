@@ -43,8 +43,10 @@ METRIC = "Gram entries/s (n=165, chi=128), split-precision vs FP64 path on 1 GB3
 # the n=165, d=6, chi_max=128 circuit, from one ncu capture of a 192-state
 # symmetric Gram (18,336 pairs, 568.2 GB in one launch).  The roofline's
 # `traffic` scales it to the pairs of one launch; it holds only for that
-# kernel version and the split depth P=2.
+# kernel version, the split depth P=2 and the tile schedule it was taken
+# with (4 kets per tile, bands of 16 bras); another schedule reports null.
 TC_DRAM_BYTES_PER_PAIR = 568.189336e9 / 18336
+TC_TRAFFIC_SCHEDULE = {"kets_per_tile": 4, "band": 16}
 
 
 def parse():
@@ -361,7 +363,8 @@ def run_ours(a):
     else:
         launches = sum(3 + (2 if r > N else 0) for r in nrefs)
     pairs = N * (N - 1) // 2
-    traffic = TC_DRAM_BYTES_PER_PAIR * pairs if a.prec == "split" else None
+    same_schedule = schedule is not None and all(schedule[k] == v for k, v in TC_TRAFFIC_SCHEDULE.items())
+    traffic = TC_DRAM_BYTES_PER_PAIR * pairs if a.prec == "split" and same_schedule else None
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     kavg = float(np.mean(kern_ms)) if kern_ms else float("nan")
@@ -384,8 +387,10 @@ def run_ours(a):
                      "kernel": "tc_overlap_kernel", "peak_source": f"bf16_tflops_sustained ({src})",
                      "algorithmic_tflop_per_launch": flops / 1e12,
                      "kernel_ms_per_launch": kavg, "refine_ms_per_step": float(np.mean(refine_ms)),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 192-state "
-                                       "capture, per pair, times the launch's pairs",
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a 192-state "
+                                        "capture, per pair, times the launch's pairs") if traffic else
+                                       ("null: the ncu capture was taken with the schedule "
+                                        f"{TC_TRAFFIC_SCHEDULE}, this run used {schedule}"),
                      "dram_tb_per_s": (traffic / (kavg / 1000.0) / 1e12) if traffic else None,
                      "note": "algorithmic complex-MAC FLOPs; the bf16x2 split issues 3 bf16 products per "
                              "real product, so frac <= 1/3 at full tensor-pipe use"},

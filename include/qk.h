@@ -202,6 +202,40 @@ qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
                         qk_prec prec, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Tile schedule of the split-precision Gram (qk_gram with a split prec).
+ * Sec. II-D distributes square tiles of the Gram matrix over GPUs; on one
+ * GPU the kernel takes tiles of one bra and `kets_per_tile` kets (1, 2 or
+ * 4), in bands of `band` bras whose tiles run side by side and share the
+ * kets in L2.  The paper has no tuner: here the schedule is chosen by
+ * measurement.
+ *
+ * qk_tune_split times six candidate schedules (kets 4/2/1 x bands 16/64) on
+ * one sample of the Gram of (A, B) -- the pairs of the first 64 bras with
+ * the first ~160 kets, about two tiles per CTA; each candidate runs twice
+ * and its faster run counts) and keeps the fastest, the default (4 kets,
+ * bands of 16) unless another beats it by more than 3 %, for later qk_gram
+ * calls on the same A, B and split depth (cached with A's
+ * tensor-core operands, dropped by qk_mps_free(A)).  qk_gram tunes by itself
+ * when the Gram has at least 64 default tiles per CTA; smaller Grams use 4
+ * kets per tile in bands of 16 unless a schedule was tuned or set.
+ *   prec     QK_PREC_SPLIT_BF16 or QK_PREC_SPLIT_BF16X3.
+ *   kets_per_tile, band, us_per_pair   optional host outs: the chosen
+ *            schedule and its device time per pair on the sample.
+ * A schedule already cached (tuned or set) is returned without timing.
+ * Synchronises.  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT.
+ *
+ * qk_set_split_schedule fixes the schedule for (A, B, prec) instead:
+ * kets_per_tile in 1..4, band >= 1.  Every schedule computes the same
+ * entries; only their order and grouping on the GPU change.
+ * ---------------------------------------------------------------------- */
+qk_status qk_tune_split(const qk_mps_batch* A, const qk_mps_batch* B,
+                        qk_prec prec, void* stream, int32_t* kets_per_tile,
+                        int32_t* band, double* us_per_pair);
+qk_status qk_set_split_schedule(const qk_mps_batch* A, const qk_mps_batch* B,
+                                qk_prec prec, int32_t kets_per_tile,
+                                int32_t band);
+
+/* ------------------------------------------------------------------------
  * qk_gram_pairs_noalloc - the FP64 pair overlaps of qk_gram_pairs
  * (QK_PREC_FP64) without any device or host allocation inside the call.
  * The paper has no counterpart: this entry point exists for callers that

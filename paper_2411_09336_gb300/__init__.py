@@ -60,6 +60,8 @@ _sig("qk_mps_save", [_vp, _vp, _i64])
 _sig("qk_mps_load", [_vp, _i64, _vp, C.POINTER(_vp)])
 _sig("qk_last_profile", [C.POINTER(_f64), C.POINTER(_f64), C.POINTER(_f64)])
 _sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
+_sig("qk_tune_split", [_vp, _vp, C.c_int, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_f64)])
+_sig("qk_set_split_schedule", [_vp, _vp, C.c_int, _i32, _i32])
 
 
 class QKError(RuntimeError):
@@ -273,6 +275,23 @@ def qk_gram_pairs_noalloc(A: MPSBatch, B: MPSBatch, pairs, out, stream=None):
                                       _stream_ptr(stream)), "qk_gram_pairs_noalloc")
     return out
 
+
+
+def qk_tune_split(A: MPSBatch, B: MPSBatch | None = None, prec: str = "split", stream=None) -> dict:
+    """Tile schedule of the split Gram of (A, B) chosen by timing candidates on
+    a sample (cached; a cached or set schedule is returned as is)."""
+    B = A if B is None else B
+    k, b, us = _i32(), _i32(), _f64()
+    _check(_lib.qk_tune_split(A.handle, B.handle, _PREC[prec], _stream_ptr(stream), C.byref(k), C.byref(b),
+                              C.byref(us)), "qk_tune_split")
+    return {"kets_per_tile": k.value, "band": b.value, "us_per_pair": us.value}
+
+
+def qk_set_split_schedule(A: MPSBatch, B: MPSBatch | None = None, prec: str = "split", kets_per_tile: int = 4,
+                          band: int = 16) -> None:
+    B = A if B is None else B
+    _check(_lib.qk_set_split_schedule(A.handle, B.handle, _PREC[prec], int(kets_per_tile), int(band)),
+           "qk_set_split_schedule")
 
 _sig("qk_surrogate_create", [_i32, _i32, _u64, C.POINTER(_vp)])
 _sig("qk_surrogate_free", [_vp])

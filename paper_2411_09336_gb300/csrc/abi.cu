@@ -397,6 +397,33 @@ extern "C" qk_status qk_gram(const qk_mps_batch* A, const qk_mps_batch* B, doubl
   return rc;
 }
 
+extern "C" qk_status qk_tune_split(const qk_mps_batch* A, const qk_mps_batch* B, qk_prec prec, void* stream,
+                                   int32_t* kets_per_tile, int32_t* band, double* us_per_pair) {
+  qk_status rc = check_pair(A, B, "qk_tune_split");
+  if (rc != QK_OK) return rc;
+  if (prec != QK_PREC_SPLIT_BF16 && prec != QK_PREC_SPLIT_BF16X3)
+    return fail(QK_ERR_INVALID_ARG, "qk_tune_split: prec must be a split precision");
+  int32_t k = 0, b = 0;
+  double us = 0.0;
+  rc = split_schedule(split_parts(prec), A, B, (cudaStream_t)stream, true, &k, &b, &us);
+  if (rc != QK_OK) return rc;
+  if (kets_per_tile) *kets_per_tile = k;
+  if (band) *band = b;
+  if (us_per_pair) *us_per_pair = us;
+  return QK_OK;
+}
+
+extern "C" qk_status qk_set_split_schedule(const qk_mps_batch* A, const qk_mps_batch* B, qk_prec prec,
+                                           int32_t kets_per_tile, int32_t band) {
+  qk_status rc = check_pair(A, B, "qk_set_split_schedule");
+  if (rc != QK_OK) return rc;
+  if (prec != QK_PREC_SPLIT_BF16 && prec != QK_PREC_SPLIT_BF16X3)
+    return fail(QK_ERR_INVALID_ARG, "qk_set_split_schedule: prec must be a split precision");
+  if (kets_per_tile < 1 || kets_per_tile > 4 || band < 1)
+    return fail(QK_ERR_INVALID_ARG, "qk_set_split_schedule: kets_per_tile in 1..4, band >= 1");
+  return set_split_schedule(split_parts(prec), A, B, kets_per_tile, band);
+}
+
 extern "C" qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B, const int32_t* pairs,
                                    int64_t P, double* K_out, qk_prec prec, void* stream) {
   qk_status rc = check_pair(A, B, "qk_gram_pairs");

@@ -31,6 +31,7 @@ void timer_begin_call() {
 void timer_set_phase(int phase) { g_phase = phase; }
 void timer_mark(bool end, cudaStream_t st) {
   const int p = g_phase;
+  if (p < 0 || p > 1) return;  // launches outside the timed phases
   if (!end) {
     if (g_nspan[p] >= kSpans) return;  // further spans are not timed
     int i = g_nspan[p];

@@ -4,8 +4,8 @@
 // in two half-steps, both complex GEMMs:
 //   HS1 (ket side):  T_s[a][b'] = sum_b E[a][b] B_j[s][b][b']
 //   HS2 (bra side):  E'[a'][b'] = sum_{s,a} conj(A_i[s][a][a']) T_s[a][b']
-// A CTA takes one bra i and up to kG kets; HS2 stacks the kets' columns so
-// the bra tensor is read once for all of them.  Operands as GEMM factors:
+// A CTA takes one bra i and up to kG kets (the tile schedule's choice);
+// HS2 stacks the kets' columns so the bra tensor is read once for all of them.  Operands as GEMM factors:
 //   HS1: D1[(s,b'), a]   = Bt_j[(s,b'), b] . Et[b, a]        (A static, B = E)
 //   HS2: D2[a', (j,b')]  = Ah_i[a', (s,a)] . T[(s,a), (j,b')] (A static, B = T)
 // Every operand is stored K-major in 16-wide K chunks of 8x(16 B) core
@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <vector>
 
 #include "qk_internal.h"
@@ -39,7 +40,7 @@ qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kG = 4;            // kets per tile
+constexpr int kG = 4;            // kets per tile at most
 // Residency: QK_TC_CTAS CTAs per SM share its 512 TMEM columns and shared
 // memory; the N of one MMA (kNMax) is sized so re and im accumulators fit.
 #ifndef QK_TC_CTAS
@@ -307,6 +308,7 @@ struct TcArgs {
   const char* b_arena;
   int n;
   int mode;                  // 0 symmetric full, 1 rectangular full, 2 pair list
+  int kets;                  // kets per tile, 1..kG (modes 0/1)
   int64_t n_tiles;
   const int32_t* tiles;      // modes 0/1: (bra i, first ket j0) per tile, banded order
   int NA, NB;
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   const uint32_t ring_bytes = Stage<P>::ring;
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
-  char* T_buf = scr + (int64_t)kG * a.et_stride;
+  char* T_buf = scr + (int64_t)a.kets * a.et_stride;
 
   while (true) {
     if (tid == 0) sh.tile = (int64_t)atomicAdd(a.queue, 1ull);
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
       i = a.tiles[2 * tile];
       const int j0 = a.tiles[2 * tile + 1];
       // symmetric: only kets above the diagonal (the diagonal runs in FP64)
-      for (int j = (a.mode == 0 ? max(j0, i + 1) : j0); j < min(j0 + kG, a.NB); ++j) {
+      for (int j = (a.mode == 0 ? max(j0, i + 1) : j0); j < min(j0 + a.kets, a.NB); ++j) {
         jj[nk] = j;
         outp[nk] = (int64_t)i * a.ldk + j;
         ++nk;
@@ -686,9 +688,47 @@ struct TcArena {
   int64_t* d_ah = nullptr;
   int64_t bytes = 0;
 };
+// Tile schedule of the full-Gram modes: kets per tile and bras per band.
+struct TcSchedule {
+  int kets = kG;
+  int band = 16;
+};
+// A schedule chosen by measurement for (this batch as A, B, split depth, mode).
+struct TcTuned {
+  const qk_mps_batch* B;
+  int P, mode;
+  TcSchedule sch;
+  double us_per_pair;
+};
 struct TcCache {
   TcArena part[2];
+  std::vector<TcTuned> tuned;
 };
+
+// Tiles (bra i, first ket j0) of the pairs with i < i_lim and j0 < j_lim, in
+// bands of sch.band bras; within a band the ket groups are the outer loop,
+// so the CTAs running at the same time share kets (and bras) in L2.
+// Symmetric (mode 0): strict upper triangle only.  Returns the number of
+// pairs the tiles cover.
+int64_t make_tiles(int mode, int64_t NB, const TcSchedule& sch, int64_t i_lim, int64_t j_lim,
+                   std::vector<int32_t>& tiles) {
+  tiles.clear();
+  int64_t pairs = 0;
+  for (int64_t i0 = 0; i0 < i_lim; i0 += sch.band) {
+    const int64_t i1 = std::min<int64_t>(i_lim, i0 + sch.band);
+    const int64_t jstart = mode == 0 ? i0 + 1 : 0;
+    for (int64_t j0 = jstart; j0 < j_lim; j0 += sch.kets)
+      for (int64_t i = i0; i < i1; ++i) {
+        const int64_t jend = std::min<int64_t>(j0 + sch.kets, NB);
+        const int64_t jbeg = mode == 0 ? std::max<int64_t>(j0, i + 1) : j0;
+        if (jend <= jbeg) continue;  // no ket above the diagonal
+        tiles.push_back((int32_t)i);
+        tiles.push_back((int32_t)j0);
+        pairs += jend - jbeg;
+      }
+  }
+  return pairs;
+}
 
 template <int P>
 qk_status ensure_tc_arena(qk_mps_batch* b, cudaStream_t st) {
@@ -748,9 +788,12 @@ qk_status ensure_tc_arena(qk_mps_batch* b, cudaStream_t st) {
 
 // Enqueues the kernel on `st` without waiting for it; *err_out receives the
 // device error word for tc_finish (nullptr when nothing was launched).
+// Modes 0/1 cover the tiles of make_tiles(sch, i_lim, j_lim); the full Gram
+// is i_lim = N_A, j_lim = N_B.
 template <int P>
 qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, const int32_t* d_pairs,
-                    int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st, int** err_out) {
+                    int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st, int** err_out,
+                    const TcSchedule& sch, int64_t i_lim, int64_t j_lim) {
   *err_out = nullptr;
   constexpr int kPlanes = 2 * P;
   qk_status rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(A), st);
@@ -762,34 +805,25 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   int dev = 0, sms = 0;
   QK_CUDA(cudaGetDevice(&dev));
   QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // tiles: (bra i, kets j0..j0+kG-1), in bands of kBand bras; within a band
-  // the ket groups are the outer loop, so the CTAs running at the same time
-  // share kets (and bras) in L2.  Symmetric: strict upper triangle only.
-  constexpr int kBand = 16;
   std::vector<int32_t> tiles;
   int64_t n_tiles = 0;
+  const int kets = mode == 2 ? 1 : std::max(1, std::min(kG, sch.kets));
   if (mode == 2) {
     n_tiles = P_pairs;
   } else {
-    for (int64_t i0 = 0; i0 < A->N; i0 += kBand) {
-      const int64_t i1 = std::min<int64_t>(A->N, i0 + kBand);
-      const int64_t jstart = mode == 0 ? i0 + 1 : 0;
-      for (int64_t j0 = jstart; j0 < B->N; j0 += kG)
-        for (int64_t i = i0; i < i1; ++i) {
-          if (mode == 0 && std::min<int64_t>(j0 + kG, B->N) <= i + 1) continue;  // no ket above the diagonal
-          tiles.push_back((int32_t)i);
-          tiles.push_back((int32_t)j0);
-        }
-    }
+    TcSchedule s2 = sch;
+    s2.kets = kets;
+    s2.band = std::max(1, sch.band);
+    make_tiles(mode, B->N, s2, std::min<int64_t>(i_lim, A->N), std::min<int64_t>(j_lim, B->N), tiles);
     n_tiles = (int64_t)tiles.size() / 2;
   }
   if (n_tiles == 0) return QK_OK;
-  // scratch: kG Et blocks (<= 128 x 128) + T (<= 128 rows x 256 K), bf16 planes
+  // scratch: `kets` Et blocks (<= 128 x 128) + T (<= 128 rows x 256 K), bf16 planes
   const int chi = std::max(A->chi_cap, B->chi_cap);
   const int cp = pad16(chi);
   const int64_t et_stride = (int64_t)cp * cp * 2 * kPlanes + 256;
   const int64_t t_bytes = (int64_t)128 * 2 * cp * 2 * kPlanes;
-  const int64_t stride = ((kG * et_stride + t_bytes) + 1023) & ~int64_t(1023);
+  const int64_t stride = ((kets * et_stride + t_bytes) + 1023) & ~int64_t(1023);
   const int64_t ctas = std::min<int64_t>((int64_t)Stage<P>::ctas_per_sm * sms, n_tiles);
   char* scratch = nullptr;
   int32_t* d_tiles = nullptr;
@@ -813,6 +847,7 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.b_arena = cb.arena;
   a.n = A->n;
   a.mode = mode;
+  a.kets = kets;
   a.n_tiles = n_tiles;
   a.tiles = d_tiles;
   a.NA = (int)A->N;
@@ -857,9 +892,108 @@ qk_status tc_finish(int* err, cudaStream_t st) {
 
 qk_status launch_tc_parts(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode,
                           const int32_t* d_pairs, int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st,
-                          int** err_out) {
-  return parts == 3 ? launch_tc<3>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out)
-                    : launch_tc<2>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out);
+                          int** err_out, const TcSchedule& sch = TcSchedule(), int64_t i_lim = INT64_MAX,
+                          int64_t j_lim = INT64_MAX) {
+  return parts == 3 ? launch_tc<3>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out, sch, i_lim, j_lim)
+                    : launch_tc<2>(A, B, mode, d_pairs, P_pairs, dK, ldk, st, err_out, sch, i_lim, j_lim);
+}
+
+// ---- schedule tuning ------------------------------------------------------
+// Candidate schedules are timed on one sample of the Gram: the pairs with bra
+// i < 64 and first ket j0 < i_lim + 160 (symmetric) or < 160, i.e. ~2 tiles per
+// CTA at 4 kets per tile, enough to fill every SM twice.  Each candidate runs
+// twice (the first warms L2 and the instruction cache) and the faster run
+// counts; the result is cached on A's operand cache for (B, P, mode).
+constexpr int kTuneBras = 64, kTuneKets = 160;
+constexpr int kTuneCands = 6;
+const TcSchedule kCands[kTuneCands] = {{4, 16}, {2, 16}, {1, 16}, {4, 64}, {2, 64}, {1, 64}};
+// A candidate replaces the default (the first) only when it is faster by
+// more than the sample's run-to-run noise.
+constexpr double kTuneMargin = 0.97;
+
+// Full Grams at least this many default tiles per CTA are tuned on the fly.
+constexpr int64_t kTuneMinTilesPerCta = 64;
+
+qk_status tune_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode, cudaStream_t st,
+                        TcSchedule* best, double* best_us_per_pair) {
+  const int64_t i_lim = std::min<int64_t>(A->N, kTuneBras);
+  const int64_t j_lim = std::min<int64_t>(B->N, (mode == 0 ? i_lim : 0) + kTuneKets);
+  // a scratch K holding every row and column the sample writes (the
+  // symmetric mirror writes rows j < j_lim + kG)
+  const int64_t rows = std::min<int64_t>(A->N, std::max<int64_t>(i_lim, j_lim + kG));
+  if (rows == 0 || B->N == 0) return QK_OK;  // nothing to time: the default stands
+  double* Ks = nullptr;
+  QK_CUDA(cudaMallocAsync(&Ks, sizeof(double) * rows * B->N, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  qk_status rc = QK_OK;
+  double best_us = 0.0, default_us = 0.0;
+  std::vector<int32_t> tiles;
+  timer_set_phase(2);  // not one of the call's timed phases
+  for (int c = 0; c < kTuneCands && rc == QK_OK; ++c) {
+    const int64_t pairs = make_tiles(mode, B->N, kCands[c], i_lim, j_lim, tiles);
+    if (pairs == 0) continue;
+    float ms_min = 0.f;
+    for (int rep = 0; rep < 2 && rc == QK_OK; ++rep) {
+      int* err = nullptr;
+      cudaEventRecord(e0, st);
+      rc = launch_tc_parts(parts, A, B, mode, nullptr, 0, Ks, B->N, st, &err, kCands[c], i_lim, j_lim);
+      cudaEventRecord(e1, st);
+      qk_status rc2 = tc_finish(err, st);  // synchronises
+      if (rc == QK_OK) rc = rc2;
+      float ms = 0.f;
+      if (rc == QK_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && (rep == 0 || ms < ms_min))
+        ms_min = ms;
+    }
+    const double us = 1000.0 * ms_min / (double)pairs;
+    if (rc != QK_OK) break;
+    if (c == 0) {
+      best_us = default_us = us;
+      *best = kCands[0];
+    } else if (us < best_us && us < kTuneMargin * default_us) {
+      best_us = us;
+      *best = kCands[c];
+    }
+  }
+  timer_set_phase(0);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(Ks, st);
+  if (best_us_per_pair) *best_us_per_pair = best_us;
+  return rc;
+}
+
+// The schedule for a full Gram of (A, B): the cached choice, else a tuned
+// one when the Gram is large enough to repay the sample, else the default.
+qk_status schedule_for(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode, cudaStream_t st,
+                       bool force, TcSchedule* out, double* us_per_pair) {
+  *out = TcSchedule();
+  if (us_per_pair) *us_per_pair = 0.0;
+  TcCache* c = (TcCache*)A->tc_cache;
+  if (c)
+    for (const TcTuned& t : c->tuned)
+      if (t.B == B && t.P == parts && t.mode == mode) {
+        *out = t.sch;
+        if (us_per_pair) *us_per_pair = t.us_per_pair;
+        return QK_OK;
+      }
+  if (!force) {
+    int dev = 0, sms = 0;
+    QK_CUDA(cudaGetDevice(&dev));
+    QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const double pairs = mode == 0 ? 0.5 * (double)A->N * (double)(A->N - 1) : (double)A->N * (double)B->N;
+    if (pairs / kG < (double)kTuneMinTilesPerCta * 4 * sms) return QK_OK;
+  }
+  TcSchedule best;
+  double us = 0.0;
+  qk_status rc = tune_schedule(parts, A, B, mode, st, &best, &us);
+  if (rc != QK_OK) return rc;
+  c = (TcCache*)A->tc_cache;  // created by the tuning launches
+  if (c) c->tuned.push_back({B, parts, mode, best, us});
+  *out = best;
+  if (us_per_pair) *us_per_pair = us;
+  return QK_OK;
 }
 
 }  // namespace
@@ -876,12 +1010,44 @@ void free_tc_cache(qk_mps_batch* b) {
   b->tc_cache = nullptr;
 }
 
+qk_status split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B, cudaStream_t st,
+                         bool force, int32_t* kets, int32_t* band, double* us_per_pair) {
+  TcSchedule sch;
+  qk_status rc = schedule_for(parts, A, B, A == B ? 0 : 1, st, force, &sch, us_per_pair);
+  if (rc != QK_OK) return rc;
+  if (kets) *kets = sch.kets;
+  if (band) *band = sch.band;
+  return QK_OK;
+}
+
+qk_status set_split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int32_t kets,
+                             int32_t band) {
+  qk_mps_batch* a = const_cast<qk_mps_batch*>(A);
+  if (!a->tc_cache) a->tc_cache = new TcCache();
+  TcCache* c = (TcCache*)a->tc_cache;
+  const int mode = A == B ? 0 : 1;
+  TcSchedule sch;
+  sch.kets = kets;
+  sch.band = band;
+  for (TcTuned& t : c->tuned)
+    if (t.B == B && t.P == parts && t.mode == mode) {
+      t.sch = sch;
+      t.us_per_pair = 0.0;
+      return QK_OK;
+    }
+  c->tuned.push_back({B, parts, mode, sch, 0.0});
+  return QK_OK;
+}
+
 qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK, int64_t ldk,
                      double refine_floor, cudaStream_t st, int64_t* n_refined) {
   const bool sym = (A == B);
   int64_t n_diag = 0;
   int* tc_err = nullptr;
-  qk_status rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st, &tc_err);
+  TcSchedule sch;
+  qk_status rc = schedule_for(parts, A, B, sym ? 0 : 1, st, false, &sch, nullptr);
+  if (rc != QK_OK) return rc;
+  rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st, &tc_err, sch);
   if (rc == QK_OK && sym) {
     // The diagonal (K_ii ~ 1, above the refinement ceiling by construction)
     // comes from the isometry-defect recursion, which needs no FP64 sweep for

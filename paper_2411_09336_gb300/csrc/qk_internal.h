@@ -81,6 +81,13 @@ void free_tc_cache(qk_mps_batch* b);
 // K[i*ldk + i] = |<psi_i|psi_i>|^2 for all states of a batch: the
 // isometry-defect recursion for left-canonical complex64 states, the FP64
 // sweep for the rest (their count in *n_fp64).  Synchronises the stream.
+// Tile schedule of the split kernel's full-Gram modes for (A, B): the cached
+// or set one, else (force, or a Gram large enough) one chosen by timing
+// candidates on a sample; else the default (4 kets per tile, bands of 16).
+qk_status split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B, cudaStream_t st,
+                         bool force, int32_t* kets, int32_t* band, double* us_per_pair);
+qk_status set_split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int32_t kets,
+                             int32_t band);
 qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st,
                              int64_t* n_fp64);
 }  // namespace qk

@@ -153,3 +153,34 @@ def test_self_overlaps_defect_recursion_and_fallback(qk):
         assert np.array_equal(d[exact], d64[exact])
         assert np.max(np.abs(d - d64) / np.maximum(d64, 1.0)) <= 1e-9
         assert nref >= len(states)
+
+
+def test_split_schedules_agree_and_tuner(qk):
+    """Every tile schedule (kets per tile x bras per band) computes the same
+    entries, symmetric and rectangular; the tuner picks one of its
+    candidates, caches it, and qk_gram then runs with it."""
+    states = ragged_states(40, 14, seed=33)
+    A = qk.qk_mps_import(states, store="c64")
+    B = qk.qk_mps_import(states[:17], store="c64")
+    K0 = qk.qk_gram(A, prec="split")[0].cpu().numpy()
+    R0 = qk.qk_gram(A, B, prec="split")[0].cpu().numpy()
+    ref = overlap.gram([mps.round_sites(s, "c64") for s in states])
+    check(K0, ref)
+    for kets in (1, 2, 3, 4):
+        for band in (1, 16, 64):
+            qk.qk_set_split_schedule(A, prec="split", kets_per_tile=kets, band=band)
+            qk.qk_set_split_schedule(A, B, prec="split", kets_per_tile=kets, band=band)
+            K = qk.qk_gram(A, prec="split")[0].cpu().numpy()
+            R = qk.qk_gram(A, B, prec="split")[0].cpu().numpy()
+            assert np.max(np.abs(K - K0)) <= 1e-12, (kets, band)
+            assert np.max(np.abs(R - R0)) <= 1e-12, (kets, band)
+    A2 = qk.qk_mps_import(states, store="c64")  # nothing cached yet
+    t = qk.qk_tune_split(A2, prec="split")
+    assert t["kets_per_tile"] in (1, 2, 4) and t["band"] in (16, 64) and t["us_per_pair"] > 0
+    assert qk.qk_tune_split(A2, prec="split") == t  # cached, not re-timed
+    K2 = qk.qk_gram(A2, prec="split")[0].cpu().numpy()
+    assert np.max(np.abs(K2 - K0)) <= 1e-12
+    with pytest.raises(qk.QKError):
+        qk.qk_set_split_schedule(A, prec="split", kets_per_tile=5)
+    with pytest.raises(qk.QKError):
+        qk.qk_tune_split(A, prec="fp64")
