@@ -49,6 +49,17 @@ TC_DRAM_BYTES_PER_PAIR = 568.189336e9 / 18336
 TC_TRAFFIC_SCHEDULE = {"kets_per_tile": 4, "band": 16}
 
 
+def roofline_traffic(prec, schedule, pairs):
+    """DRAM bytes of one tensor-core launch over `pairs` pairs, from the ncu
+    per-pair figure; None unless the run used the captured depth and tile
+    schedule."""
+    if prec != "split" or not schedule:
+        return None
+    if any(schedule.get(k) != v for k, v in TC_TRAFFIC_SCHEDULE.items()):
+        return None
+    return TC_DRAM_BYTES_PER_PAIR * pairs
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -363,8 +374,7 @@ def run_ours(a):
     else:
         launches = sum(3 + (2 if r > N else 0) for r in nrefs)
     pairs = N * (N - 1) // 2
-    same_schedule = schedule is not None and all(schedule[k] == v for k, v in TC_TRAFFIC_SCHEDULE.items())
-    traffic = TC_DRAM_BYTES_PER_PAIR * pairs if a.prec == "split" and same_schedule else None
+    traffic = roofline_traffic(a.prec, schedule, pairs)
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     kavg = float(np.mean(kern_ms)) if kern_ms else float("nan")

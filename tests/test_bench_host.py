@@ -72,3 +72,12 @@ def test_two_gloo_ranks():
     res.sort()
     assert res[0][1] == res[1][1] == 7.25
     assert set(res[0][2]).isdisjoint(res[1][2])
+
+
+def test_roofline_traffic_only_for_the_captured_schedule():
+    sch = dict(bench.TC_TRAFFIC_SCHEDULE)
+    assert bench.roofline_traffic("split", sch, 10) == bench.TC_DRAM_BYTES_PER_PAIR * 10
+    assert bench.roofline_traffic("split", {**sch, "kets_per_tile": 1}, 10) is None
+    assert bench.roofline_traffic("split_bf16x3", sch, 10) is None
+    assert bench.roofline_traffic("fp64", None, 10) is None
+    assert bench.roofline_traffic("split", {**sch, "us_per_pair": 7.0}, 10) is not None
