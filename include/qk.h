@@ -215,7 +215,9 @@ qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
  * and its faster run counts) and keeps the fastest, the default (4 kets,
  * bands of 16) unless another beats it by more than 3 %, for later qk_gram
  * calls on the same A, B and split depth (cached with A's
- * tensor-core operands, dropped by qk_mps_free(A)).  qk_gram tunes by itself
+ * tensor-core operands, dropped by qk_mps_free(A), and for the rest of the
+ * process for any Gram of the same shape: device, N_A, N_B, n, largest bond
+ * dimensions, split depth, symmetric or not).  qk_gram tunes by itself
  * when the Gram has at least 64 default tiles per CTA; smaller Grams use 4
  * kets per tile in bands of 16 unless a schedule was tuned or set.
  *   prec     QK_PREC_SPLIT_BF16 or QK_PREC_SPLIT_BF16X3.

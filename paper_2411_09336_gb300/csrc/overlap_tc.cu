@@ -27,6 +27,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "qk_internal.h"
@@ -966,6 +969,17 @@ qk_status tune_schedule(int parts, const qk_mps_batch* A, const qk_mps_batch* B,
 
 // The schedule for a full Gram of (A, B): the cached choice, else a tuned
 // one when the Gram is large enough to repay the sample, else the default.
+// Tuned schedules by the shape of the Gram (device, N_A, N_B, n, largest
+// bonds, split depth, mode), so that a new batch of the same shape -- a
+// reloaded or re-rotated copy -- reuses the choice without timing again.
+using TuneKey = std::tuple<int, int64_t, int64_t, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<TcSchedule, double>> g_tuned;
+
+TuneKey tune_key(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode) {
+  return TuneKey(A->device, A->N, B->N, A->n, A->chi_cap, B->chi_cap, parts, mode);
+}
+
 qk_status schedule_for(int parts, const qk_mps_batch* A, const qk_mps_batch* B, int mode, cudaStream_t st,
                        bool force, TcSchedule* out, double* us_per_pair) {
   *out = TcSchedule();
@@ -978,6 +992,15 @@ qk_status schedule_for(int parts, const qk_mps_batch* A, const qk_mps_batch* B, 
         if (us_per_pair) *us_per_pair = t.us_per_pair;
         return QK_OK;
       }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(parts, A, B, mode));
+    if (it != g_tuned.end()) {
+      *out = it->second.first;
+      if (us_per_pair) *us_per_pair = it->second.second;
+      return QK_OK;
+    }
+  }
   if (!force) {
     int dev = 0, sms = 0;
     QK_CUDA(cudaGetDevice(&dev));
@@ -991,6 +1014,10 @@ qk_status schedule_for(int parts, const qk_mps_batch* A, const qk_mps_batch* B, 
   if (rc != QK_OK) return rc;
   c = (TcCache*)A->tc_cache;  // created by the tuning launches
   if (c) c->tuned.push_back({B, parts, mode, best, us});
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(parts, A, B, mode)] = {best, us};
+  }
   *out = best;
   if (us_per_pair) *us_per_pair = us;
   return QK_OK;
