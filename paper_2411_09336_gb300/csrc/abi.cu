@@ -147,7 +147,12 @@ extern "C" qk_status qk_build_states(const double* X, int64_t N, int32_t n, int3
   qk_status rc = to_device(X, xb, st, &dX, &owned);
   if (rc != QK_OK) return rc;
   qk_mps_batch* b = new qk_mps_batch();
-  QK_CUDA(cudaGetDevice(&b->device));
+  cudaError_t de = cudaGetDevice(&b->device);
+  if (de != cudaSuccess) {
+    delete b;
+    if (owned) cudaFreeAsync(owned, st);
+    return cuda_fail(de, "cudaGetDevice");
+  }
   b->N = N;
   b->n = n;
   b->store = store;
@@ -227,7 +232,6 @@ extern "C" qk_status qk_mps_import(int64_t N, int32_t n, const int32_t* bond_dim
   // the import layout is [a][q][b]; the device layout is [q][a][b]
   {
     std::vector<char> perm(total);
-    size_t s0 = 0;
     for (int64_t s = 0; s < N; ++s)
       for (int k = 0; k < n; ++k) {
         int ca = bond_dims[s * (n + 1) + k], cb = bond_dims[s * (n + 1) + k + 1];
@@ -237,7 +241,6 @@ extern "C" qk_status qk_mps_import(int64_t N, int32_t n, const int32_t* bond_dim
           for (int q = 0; q < 2; ++q)
             for (int bb = 0; bb < cb; ++bb)
               memcpy(o + ((q * ca + a) * cb + bb) * eb, in + ((a * 2 + q) * cb + bb) * eb, eb);
-        (void)s0;
       }
     host.swap(perm);
   }
@@ -248,9 +251,10 @@ extern "C" qk_status qk_mps_import(int64_t N, int32_t n, const int32_t* bond_dim
   if ((e = cudaMalloc(&b->d_dims, sizeof(int32_t) * N * (n + 1))) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   if ((e = cudaMalloc(&b->d_site_ptr, sizeof(uint64_t) * N * n)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
   if ((e = cudaMalloc(&b->d_trunc_w, sizeof(double) * N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
-  cudaMemcpy(b->d_dims, bond_dims, sizeof(int32_t) * N * (n + 1), cudaMemcpyHostToDevice);
-  cudaMemcpy(b->d_site_ptr, ptrs.data(), sizeof(uint64_t) * N * n, cudaMemcpyHostToDevice);
-  cudaMemset(b->d_trunc_w, 0, sizeof(double) * N);
+  if ((e = cudaMemcpy(b->d_dims, bond_dims, sizeof(int32_t) * N * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_site_ptr, ptrs.data(), sizeof(uint64_t) * N * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->d_trunc_w, 0, sizeof(double) * N)) != cudaSuccess)
+    return bail(cuda_fail(e, "qk_mps_import tables"));
   qk_status rc = finish_batch(b, st);
   if (rc != QK_OK) return bail(rc);
   *out = b;
