@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) build_kernel(BuildArgs a) {
 
 }  // namespace
 
-// Host driver: validates nothing (qk_build_states does), sizes the workspace,
+// Host side: validates nothing (qk_build_states does), sizes the workspace,
 // launches the persistent kernel, grows the pool for states that did not fit.
 qk_status build_states_device(const double* dX, int64_t N, int n, int d, int reps,
                               double gamma, int chi_max, double eps, qk_store store,
