@@ -71,13 +71,13 @@ __host__ __device__ inline int ntiles_of(int rows) { return rows <= 64 ? 1 : (ro
 // rows stored for M tile t of a static operand with `rows` rows (no padding)
 __host__ __device__ inline int tile_rows(int rows, int t) { return rows - 128 * t < 128 ? rows - 128 * t : 128; }
 
-// element offset of (row, k) in a dynamic B operand: [kchunk][64-row tile]
-// [plane][rows_t x 16], rows_t = min(64, rows - 64 t), so that the rows of
-// one N slice of one chunk form one contiguous block
+// element offset of (row, k) in a dynamic B operand: [kchunk][kNMax-row tile]
+// [plane][rows_t x 16], rows_t = min(kNMax, rows - kNMax t), so that the rows
+// of one N slice of one chunk form one contiguous block
 template <int PL>
 __host__ __device__ inline int64_t dyn_off(int row, int k, int plane, int rows) {
   const int kc = k >> 4, k16 = k & 15;
-  const int t = row >> 6, r = row & 63;
+  const int t = (int)((unsigned)row / kNMax), r = (int)((unsigned)row % kNMax);  // row >= 0
   const int rows_t = min(kNMax, rows - kNMax * t);
   return (int64_t)kc * PL * rows * 16 + (int64_t)t * PL * kNMax * 16 + (int64_t)plane * rows_t * 16 +
          (r >> 3) * 128 + (k16 >> 3) * 64 + (r & 7) * 8 + (k16 & 7);
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     } else {
       i = a.tiles[2 * tile];
       const int j0 = a.tiles[2 * tile + 1];
-      // symmetric: only kets above the diagonal (the diagonal runs in FP64)
+      // symmetric: only kets above the diagonal (the self-overlaps run separately)
       for (int j = (a.mode == 0 ? max(j0, i + 1) : j0); j < min(j0 + a.kets, a.NB); ++j) {
         jj[nk] = j;
         outp[nk] = (int64_t)i * a.ldk + j;
@@ -515,8 +515,8 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
       const int ap = pad16(da[k]), ap1 = pad16(da[k + 1]);
       int q0 = 0;
       while (q0 < nk) {
-        // group kets while their stacked columns fit one MMA (<= 64); a ket
-        // wider than 64 forms a group of its own, split into 64-row slices
+        // group kets while their stacked columns fit one MMA (<= kNMax); a
+        // ket wider than kNMax forms a group of its own, split into slices
         int q1 = q0, ntot = 0;
         int nb[kG];
         while (q1 < nk) {
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
             }
           }
         }
-        // ---- HS2 for the group: D2[a', (j,b')] over 64-row slices of T
+        // ---- HS2 for the group: D2[a', (j,b')] over kNMax-row slices of T
         {
           const int mr = mrows_of(ap1);
           const char* ah = a.a_arena + a.a_ah[(int64_t)i * n + k];
@@ -646,7 +646,7 @@ __global__ void select_refine_kernel(const double* K, int64_t ldk, int NA, int N
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / NB), j = (int)(e % NB);
-    if (sym && j <= i) continue;  // the diagonal is already FP64
+    if (sym && j <= i) continue;  // the self-overlaps are computed separately
     const double v = K[(int64_t)i * ldk + j];
     if (v < floor_v || v > ceil_v) {
       unsigned long long p = atomicAdd(count, 1ull);
