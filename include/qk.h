@@ -209,9 +209,10 @@ qk_status qk_gram_pairs(const qk_mps_batch* A, const qk_mps_batch* B,
  * kets in L2.  The paper has no tuner: here the schedule is chosen by
  * measurement.
  *
- * qk_tune_split times six candidate schedules (kets 4/2/1 x bands 16/64) on
- * one sample of the Gram of (A, B) -- the pairs of the first 64 bras with
- * the first ~160 kets, about two tiles per CTA; each candidate runs twice
+ * qk_tune_split times six candidate schedules (4 kets in bands of 16, 2 in
+ * bands of 64, 1 in bands of 16/32/64/128) on one sample of the Gram of
+ * (A, B) -- the pairs of the first 128 bras with the first ~290 kets (160
+ * when B != A), at least four tiles per CTA; each candidate runs twice
  * and its faster run counts) and keeps the fastest, the default (4 kets,
  * bands of 16) unless another beats it by more than 3 %, for later qk_gram
  * calls on the same A, B and split depth (cached with A's

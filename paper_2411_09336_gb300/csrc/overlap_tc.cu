@@ -903,13 +903,15 @@ qk_status launch_tc_parts(int parts, const qk_mps_batch* A, const qk_mps_batch* 
 
 // ---- schedule tuning ------------------------------------------------------
 // Candidate schedules are timed on one sample of the Gram: the pairs with bra
-// i < 64 and first ket j0 < i_lim + 160 (symmetric) or < 160, i.e. ~2 tiles per
-// CTA at 4 kets per tile, enough to fill every SM twice.  Each candidate runs
-// twice (the first warms L2 and the instruction cache) and the faster run
-// counts; the result is cached on A's operand cache for (B, P, mode).
-constexpr int kTuneBras = 64, kTuneKets = 160;
+// i < 128 and first ket j0 < i_lim + 160 (symmetric) or < 160, i.e. >= 4 tiles
+// per CTA at 4 kets per tile, enough to fill every SM several times and to
+// hold the largest band.  Each candidate runs twice (the first warms L2 and
+// the instruction cache) and the faster run counts; the result is cached on
+// A's operand cache for (B, P, mode).  One ket per tile keeps the least
+// per-CTA scratch live, so the bands are explored at that width.
+constexpr int kTuneBras = 128, kTuneKets = 160;
 constexpr int kTuneCands = 6;
-const TcSchedule kCands[kTuneCands] = {{4, 16}, {2, 16}, {1, 16}, {4, 64}, {2, 64}, {1, 64}};
+const TcSchedule kCands[kTuneCands] = {{4, 16}, {2, 64}, {1, 16}, {1, 32}, {1, 64}, {1, 128}};
 // A candidate replaces the default (the first) only when it is faster by
 // more than the sample's run-to-run noise.
 constexpr double kTuneMargin = 0.97;

@@ -176,7 +176,8 @@ def test_split_schedules_agree_and_tuner(qk):
             assert np.max(np.abs(R - R0)) <= 1e-12, (kets, band)
     A2 = qk.qk_mps_import(states, store="c64")  # nothing cached yet
     t = qk.qk_tune_split(A2, prec="split")
-    assert t["kets_per_tile"] in (1, 2, 4) and t["band"] in (16, 64) and t["us_per_pair"] > 0
+    assert (t["kets_per_tile"], t["band"]) in {(4, 16), (2, 64), (1, 16), (1, 32), (1, 64), (1, 128)}
+    assert t["us_per_pair"] > 0
     assert qk.qk_tune_split(A2, prec="split") == t  # cached, not re-timed
     K2 = qk.qk_gram(A2, prec="split")[0].cpu().numpy()
     assert np.max(np.abs(K2 - K0)) <= 1e-12
