@@ -68,3 +68,24 @@ def test_bad_arguments_rejected_on_host(lib):
         assert lib.qk_last_error()
     # NULL output pointer
     assert f(X.ctypes.data, 4, 8, 1, 2, 0.5, 16, 0.0, 1, None, None, None) == 1
+
+
+def test_null_handles_rejected_on_host(lib):
+    """Entry points taking batches reject NULL handles before any CUDA call."""
+    lib.qk_last_error.restype = C.c_char_p
+    k, b = C.c_int32(), C.c_int32()
+    us = C.c_double()
+    lib.qk_tune_split.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    assert lib.qk_tune_split(None, None, 1, None, C.byref(k), C.byref(b), C.byref(us)) == 1
+    assert b"NULL" in lib.qk_last_error()
+    lib.qk_set_split_schedule.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int32, C.c_int32]
+    assert lib.qk_set_split_schedule(None, None, 1, 1, 16) == 1
+    lib.qk_gram.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_void_p,
+                            C.c_void_p]
+    assert lib.qk_gram(None, None, None, 0, 1, 0.0, None, None) == 1
+    lib.qk_mps_shape.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    assert lib.qk_mps_shape(None, None, None) == 1
+    # freeing NULL is a no-op
+    lib.qk_mps_free.argtypes = [C.c_void_p]
+    assert lib.qk_mps_free(None) == 0
