@@ -89,3 +89,20 @@ def test_null_handles_rejected_on_host(lib):
     # freeing NULL is a no-op
     lib.qk_mps_free.argtypes = [C.c_void_p]
     assert lib.qk_mps_free(None) == 0
+
+
+def test_non_finite_features_rejected_on_host(lib):
+    """A NaN or infinite feature is an argument error found on the host copy
+    of X (no state is built)."""
+    import numpy as np
+    lib.qk_last_error.restype = C.c_char_p
+    f = lib.qk_build_states
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                  C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+    out = C.c_void_p()
+    for bad in (np.nan, np.inf, -np.inf):
+        X = np.zeros((3, 6))
+        X[2, 4] = bad
+        assert f(X.ctypes.data, 3, 6, 1, 2, 0.5, 16, 0.0, 1, None, None, C.byref(out)) == 1
+        assert b"non-finite" in lib.qk_last_error()
+        assert out.value is None
