@@ -92,7 +92,9 @@ const char* qk_last_error(void);
  *            rank kept after every two-site op, in execution order;
  *            n_ops = qk_schedule_length(n, d).
  *   out      receives the new batch (free with qk_mps_free).
- * The build runs in FP64.  Two-site ops follow the SWAP-routed schedule:
+ * The build runs in FP64: every two-site op is a Householder QR with column
+ * pivoting followed by a one-sided Jacobi SVD of its R factor.  Two-site ops
+ * follow the SWAP-routed schedule:
  * for each qubit i, Rxx(i,i+t) (t < k) fused with the following SWAP, then
  * Rxx(i,i+k) and k-1 SWAPs back, k = min(d, n-1-i) (Sec. II-C).  Final
  * states are left-canonical.  Synchronises.
@@ -103,6 +105,20 @@ qk_status qk_build_states(const double* X, int64_t N, int32_t n, int32_t d,
                           int32_t reps, double gamma, int32_t chi_max,
                           double eps, qk_store store, int32_t* rank_trace,
                           void* stream, qk_mps_batch** out);
+
+/* Device-side profile of the last qk_build_states call on this thread:
+ *   kernel_ms       CUDA-event time of the build kernel launches;
+ *   phase_sm_ms     host double [6]: SM-milliseconds (clock64 cycles of each
+ *                   CTA / SM clock, summed over CTAs) spent in: theta formation
+ *                   and gate, QR with column pivoting, Jacobi sweeps, writing
+ *                   the factors (isometry + GEMM), centre moves, other (Z
+ *                   layers, packing);
+ *   ctas            CTAs launched; sweeps  Jacobi sweeps summed over all
+ *                   factorisations; factorisations  their number.
+ * Any pointer may be NULL.  No synchronisation. */
+qk_status qk_last_build_profile(double* kernel_ms, double* phase_sm_ms,
+                                int64_t* ctas, int64_t* sweeps,
+                                int64_t* factorisations);
 
 /* Number of two-site ops in one repetition: sum_i (2 min(d, n-1-i) - 1). */
 int64_t qk_schedule_length(int32_t n, int32_t d);
@@ -237,6 +253,14 @@ qk_status qk_tune_split(const qk_mps_batch* A, const qk_mps_batch* B,
 qk_status qk_set_split_schedule(const qk_mps_batch* A, const qk_mps_batch* B,
                                 qk_prec prec, int32_t kets_per_tile,
                                 int32_t band);
+
+/* Test hook for the failure path (the paper has no counterpart): when `on`,
+ * the next launch of the tensor-core overlap kernel lets one bounded wait of
+ * CTA 0 run out (a 10 ms wait on a barrier nothing arrives at, in the middle
+ * of a GEMM with bulk copies and MMAs in flight).  The CTA then drains what
+ * it issued, frees its TMEM and exits, and the call returns QK_ERR_TIMEOUT;
+ * the device stays usable.  Consumed by that launch. */
+qk_status qk_debug_stall_next_split(int32_t on);
 
 /* ------------------------------------------------------------------------
  * qk_gram_pairs_noalloc - the FP64 pair overlaps of qk_gram_pairs

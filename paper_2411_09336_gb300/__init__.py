@@ -59,7 +59,9 @@ _sig("qk_mps_blob_bytes", [_vp, C.POINTER(_i64)])
 _sig("qk_mps_save", [_vp, _vp, _i64])
 _sig("qk_mps_load", [_vp, _i64, _vp, C.POINTER(_vp)])
 _sig("qk_last_profile", [C.POINTER(_f64), C.POINTER(_f64), C.POINTER(_f64)])
+_sig("qk_last_build_profile", [C.POINTER(_f64), _vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
 _sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
+_sig("qk_debug_stall_next_split", [_i32])
 _sig("qk_tune_split", [_vp, _vp, C.c_int, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_f64)])
 _sig("qk_set_split_schedule", [_vp, _vp, C.c_int, _i32, _i32])
 
@@ -218,14 +220,38 @@ def qk_gram(A: MPSBatch, B: MPSBatch | None = None, prec: str = "fp64", refine_f
     return out, nref.value
 
 
+def _check_pairs(pairs, where: str, cuda_only: bool = False):
+    """pairs must be int32 of shape (P, 2) (a CUDA tensor when cuda_only)."""
+    dt = getattr(pairs, "dtype", None)
+    ok_dtype = dt == np.int32 or str(dt) == "torch.int32"
+    if not ok_dtype or len(pairs.shape) != 2 or pairs.shape[1] != 2:
+        raise ValueError(f"{where}: pairs must be int32 of shape (P, 2), got {dt} {tuple(pairs.shape)}")
+    if cuda_only and not getattr(pairs, "is_cuda", False):
+        raise ValueError(f"{where}: pairs must be a CUDA tensor")
+
+
+def _check_out(out, P: int, where: str, cuda_only: bool = False):
+    """out must be float64 with at least P elements (a CUDA tensor when cuda_only)."""
+    dt = getattr(out, "dtype", None)
+    if not (dt == np.float64 or str(dt) == "torch.float64"):
+        raise ValueError(f"{where}: out must be float64, got {dt}")
+    numel = out.size if isinstance(out, np.ndarray) else out.numel()
+    if numel < P:
+        raise ValueError(f"{where}: out holds {numel} values, {P} needed")
+    if cuda_only and not getattr(out, "is_cuda", False):
+        raise ValueError(f"{where}: out must be a CUDA tensor")
+
+
 def qk_gram_pairs(A: MPSBatch, B: MPSBatch, pairs, prec: str = "fp64", out=None, stream=None):
     """K[p] = |<a_{pairs[p,0]}|b_{pairs[p,1]}>|^2; pairs int32 (P, 2)."""
     import torch
     if isinstance(pairs, np.ndarray):
         pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+    _check_pairs(pairs, "qk_gram_pairs")
     P = pairs.shape[0]
     if out is None:
         out = torch.empty(P, dtype=torch.float64, device="cuda")
+    _check_out(out, P, "qk_gram_pairs")
     _check(_lib.qk_gram_pairs(A.handle, B.handle, _ptr(pairs), P, _ptr(out), _PREC[prec],
                               _stream_ptr(stream)), "qk_gram_pairs")
     return out
@@ -267,10 +293,34 @@ def qk_last_profile() -> dict:
     return {"overlap_ms": a.value, "refine_ms": b.value, "total_ms": c.value}
 
 
+def qk_debug_stall_next_split(on: bool = True) -> None:
+    """Test hook: the next tensor-core overlap launch lets one bounded wait run
+    out (the call then fails with QK_ERR_TIMEOUT; see include/qk.h)."""
+    _check(_lib.qk_debug_stall_next_split(1 if on else 0), "qk_debug_stall_next_split")
+
+
+BUILD_PHASES = ("theta", "qr", "jacobi", "factors_out", "moves", "other")
+
+
+def qk_last_build_profile() -> dict:
+    """Device profile of the last qk_build_states call: kernel milliseconds,
+    SM-milliseconds per phase (summed over CTAs), Jacobi sweeps and
+    factorisations."""
+    ms = _f64()
+    ph = np.zeros(len(BUILD_PHASES), dtype=np.float64)
+    ctas, sw, nf = _i64(), _i64(), _i64()
+    _check(_lib.qk_last_build_profile(C.byref(ms), ph.ctypes.data, C.byref(ctas), C.byref(sw), C.byref(nf)),
+           "qk_last_build_profile")
+    return {"kernel_ms": ms.value, "phase_sm_ms": dict(zip(BUILD_PHASES, ph.tolist())), "ctas": ctas.value,
+            "sweeps": sw.value, "factorisations": nf.value}
+
+
 def qk_gram_pairs_noalloc(A: MPSBatch, B: MPSBatch, pairs, out, stream=None):
     """FP64 pair overlaps into the caller's device buffer `out` with no
     allocation inside the library call (bond dimensions <= 64; pairs and out
     must be CUDA tensors).  See include/qk.h for the shared-scratch rules."""
+    _check_pairs(pairs, "qk_gram_pairs_noalloc", cuda_only=True)
+    _check_out(out, pairs.shape[0], "qk_gram_pairs_noalloc", cuda_only=True)
     _check(_lib.qk_gram_pairs_noalloc(A.handle, B.handle, _ptr(pairs), pairs.shape[0], _ptr(out),
                                       _stream_ptr(stream)), "qk_gram_pairs_noalloc")
     return out

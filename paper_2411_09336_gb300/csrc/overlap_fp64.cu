@@ -45,19 +45,19 @@ struct PairArgs {
   int sym;
   double2* scratch;        // per CTA 3 * cap
   int64_t cap;
-  int* queue;
+  unsigned long long* queue;  // work counter (64-bit: it runs past P by the CTA count)
 };
 
 template <typename C>
 __global__ void __launch_bounds__(kThreads) overlap_fp64_kernel(PairArgs a) {
-  __shared__ int s_pair;
+  __shared__ long long s_pair;
   double2* E = a.scratch + (int64_t)blockIdx.x * 3 * a.cap;
   double2* T = E + a.cap;
   double2* E2 = T + a.cap;
   const int n = a.n;
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) s_pair = atomicAdd(a.queue, 1);
+    if (threadIdx.x == 0) s_pair = (long long)atomicAdd(a.queue, 1ull);
     __syncthreads();
     const int64_t pi = s_pair;
     if (pi >= a.P) break;
@@ -166,10 +166,10 @@ qk_status overlap_fp64(const qk_mps_batch* A, const qk_mps_batch* B, const int32
   int64_t cap = 2LL * chi * chi;
   int64_t ctas = std::min<int64_t>((int64_t)sms * ctas_per_sm, P);
   double2* scratch = nullptr;
-  int* queue = nullptr;
+  unsigned long long* queue = nullptr;
   QK_CUDA(cudaMallocAsync(&scratch, sizeof(double2) * 3 * cap * ctas, st));
-  QK_CUDA(cudaMallocAsync(&queue, sizeof(int), st));
-  QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), st));
+  QK_CUDA(cudaMallocAsync(&queue, sizeof(unsigned long long), st));
+  QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st));
   PairArgs a;
   a.a_ptr = A->d_site_ptr;
   a.a_dims = A->d_dims;
@@ -288,7 +288,7 @@ extern "C" qk_status qk_gram_pairs_noalloc(const qk_mps_batch* A, const qk_mps_b
   a.sym = 0;
   a.scratch = scratch + kNoAllocCtl;
   a.cap = kNoAllocCap;
-  a.queue = reinterpret_cast<int*>(scratch);
+  a.queue = reinterpret_cast<unsigned long long*>(scratch);
   const int ctas = (int)std::min<int64_t>(std::min(kNoAllocCtas, 4 * sms), P);
   if (A->store == QK_STORE_C64)
     overlap_fp64_kernel<float2><<<ctas, kThreads, 0, st>>>(a);

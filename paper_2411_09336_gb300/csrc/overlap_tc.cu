@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -200,7 +201,7 @@ __device__ inline unsigned long long now_ns() {
 }
 
 // bounded wait on an mbarrier phase; false on timeout
-__device__ inline bool wait_bar(uint64_t* bar, uint32_t parity) {
+__device__ inline bool wait_bar(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = kTimeoutNs) {
   const uint32_t a = smem_u32(bar);
   uint32_t done = 0;
   unsigned long long t0 = 0;
@@ -215,7 +216,7 @@ __device__ inline bool wait_bar(uint64_t* bar, uint32_t parity) {
       unsigned long long t = now_ns();
       if (it == 0)
         t0 = t;
-      else if (t - t0 > kTimeoutNs)
+      else if (t - t0 > limit_ns)
         return false;
     }
   }
@@ -323,14 +324,21 @@ struct TcArgs {
   int64_t et_stride;
   unsigned long long* queue;
   int* err;
+  int stall;                 // test hook: CTA 0 lets one bounded wait run out mid-GEMM
 };
 
 constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
+
+// test hook (qk_debug_stall_next_split): the next tensor-core launch lets one
+// bounded wait run out
+std::atomic<int> g_stall_next{0};
 
 struct __align__(8) TcShared {
   uint64_t full[kSlots];
   uint64_t empty[kSlots];
   uint64_t done;
+  uint64_t drain;   // tcgen05.commit target when an aborting CTA drains its MMAs
+  uint64_t stall;   // never arrived at (test hook)
   uint32_t tmem;
   int abort;
   int64_t tile;
@@ -343,6 +351,7 @@ struct __align__(8) TcShared {
 // reclaimed in order once the MMAs that read them have completed.
 struct Ring {
   uint32_t produced = 0, released = 0;
+  uint32_t issued = 0, waited = 0;  // chunks whose copies were issued / whose copies have landed
   uint32_t head = 0, tail = 0;  // bytes ever produced / reclaimed
   uint32_t off[kSlots], len[kSlots];
 };
@@ -362,7 +371,7 @@ __device__ inline bool ring_release(TcShared& sh, Ring& r) {
 template <int P>
 __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg, const char* gA,
                          uint32_t a_bytes, int a_rows, const char* gB, uint32_t b_bytes, int64_t b_stride,
-                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b) {
+                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b, bool& stall) {
   const uint32_t id_pos = make_idesc(M, N, 0), id_neg = make_idesc(M, N, 1);
   const uint32_t t_re = sh.tmem, t_im = sh.tmem + N;
   // The MMA reads M rows of every A plane; the planes hold a_rows <= M rows,
@@ -388,6 +397,7 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
       expect_tx(&sh.full[slot], a_bytes + b_bytes);
       bulk_load(ring + off, gA + (int64_t)p * a_bytes, a_bytes, &sh.full[slot], pol_a);
       bulk_load(ring + off + a_span, gB + (int64_t)p * b_stride, b_bytes, &sh.full[slot], pol_b);
+      rg.issued = gi + 1;
       ++p;
     }
     return true;
@@ -396,7 +406,14 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
   for (int c = 0; c < nchunks; ++c) {
     const uint32_t gi = g0 + c, slot = gi % kSlots;
     if (p <= c && !top_up(gi)) return false;  // reclaims everything before chunk c
+    if (stall && c == 1) {
+      // test hook: a wait on a barrier nothing arrives at runs out while
+      // chunk 0's MMAs and the later chunks' copies are in flight
+      stall = false;
+      if (!wait_bar(&sh.stall, 0, 10000000ull)) return false;
+    }
     if (!wait_bar(&sh.full[slot], (gi / kSlots) & 1)) return false;
+    rg.waited = gi + 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // bytes per plane: A is stored with a_rows rows (rows of the M tile past
     // a_rows read other data and only feed accumulator rows that are unused)
@@ -461,6 +478,8 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.empty[s])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.drain)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.stall)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     sh.abort = 0;
   }
@@ -470,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   const uint32_t tmem = sh.tmem;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
   Ring rg;                  // operand ring (thread 0)
+  bool stall = a.stall && blockIdx.x == 0;  // test hook, first GEMM of >= 2 chunks
   const uint32_t ring_bytes = Stage<P>::ring;
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
@@ -542,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                 const char* gB = et + (int64_t)h0 * kRowBytes;
                 const int rt = tile_rows(rows, t);
                 if (!run_gemm<P>(sh, stage, ring_bytes, rg, gA, rt * kRowBytes, rt, gB, nh * kRowBytes,
-                                 (int64_t)ap * kRowBytes, bp / 16, mr, nh, pol_first, pol_last)) {
+                                 (int64_t)ap * kRowBytes, bp / 16, mr, nh, pol_first, pol_last, stall)) {
                   sh.abort = 1;
                   atomicExch(a.err, 1);
                 }
@@ -584,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
             if (tid == 0) {
               const char* gB = T_buf + (int64_t)h0 * kRowBytes;
               if (!run_gemm<P>(sh, stage, ring_bytes, rg, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytes,
-                               (int64_t)ntot * kRowBytes, (2 * ap) / 16, mr, nh, pol_first, pol_last)) {
+                               (int64_t)ntot * kRowBytes, (2 * ap) / 16, mr, nh, pol_first, pol_last, stall)) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
@@ -635,6 +655,18 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   }
 finish:
   __syncthreads();
+  if (tid == 0 && sh.abort) {
+    // An aborting CTA may still have bulk copies landing in its ring and MMAs
+    // writing its TMEM: wait (bounded) for every copy issued but not yet
+    // waited for, then for every MMA this thread issued, before the TMEM is
+    // freed and the CTA's shared memory is released.
+    for (uint32_t gi = rg.waited; gi < rg.issued; ++gi) wait_bar(&sh.full[gi % kSlots], (gi / kSlots) & 1);
+    commit(&sh.drain);
+    wait_bar(&sh.drain, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
   if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
@@ -863,6 +895,7 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.et_stride = et_stride;
   a.queue = queue;
   a.err = err;
+  a.stall = g_stall_next.exchange(0);
   const int smem = Stage<P>::ring;
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1152,3 +1185,8 @@ qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, c
 }
 
 }  // namespace qk
+
+extern "C" qk_status qk_debug_stall_next_split(int32_t on) {
+  qk::g_stall_next.store(on ? 1 : 0);
+  return QK_OK;
+}

@@ -185,3 +185,19 @@ def test_split_schedules_agree_and_tuner(qk):
         qk.qk_set_split_schedule(A, prec="split", kets_per_tile=5)
     with pytest.raises(qk.QKError):
         qk.qk_tune_split(A, prec="fp64")
+
+
+def test_bounded_wait_runs_out_and_device_stays_usable(qk):
+    """A bounded mbarrier wait that runs out (test hook: a wait on a barrier
+    nothing arrives at, with copies and MMAs in flight) makes the call fail
+    with QK_ERR_TIMEOUT; the aborting CTA drains its work and frees its TMEM,
+    so the next call on the same device is exact again."""
+    st = ragged_states(6, 12, 31, chis=(33, 40, 48))
+    A = qk.qk_mps_import(st, store="c64")
+    Kref = overlap.gram([mps.round_sites(s, "c64") for s in st])
+    qk.qk_debug_stall_next_split(True)
+    with pytest.raises(qk.QKError) as ei:
+        qk.qk_gram(A, prec="split")
+    assert ei.value.status == qk.QK_ERR_TIMEOUT
+    K, _ = qk.qk_gram(A, prec="split")
+    check(K.cpu().numpy(), Kref)

@@ -57,5 +57,35 @@ def test_noalloc_rejects_what_it_cannot_hold(qk):
     small = qk.qk_mps_import(states(3, 10, 6, (8,)), store="c64")
     with pytest.raises(qk.QKError):
         qk.qk_gram_pairs_noalloc(small, small, torch.tensor([[0, 3]], dtype=torch.int32, device="cuda"), out)
-    with pytest.raises(qk.QKError):  # host output buffer
+    with pytest.raises(ValueError):  # host output buffer
         qk.qk_gram_pairs_noalloc(small, small, dp, torch.empty(1, dtype=torch.float64))
+    two = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):  # output shorter than the pair list
+        qk.qk_gram_pairs_noalloc(small, small, two, out)
+    with pytest.raises(ValueError):  # float32 output
+        qk.qk_gram_pairs_noalloc(small, small, dp, torch.empty(1, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):  # int64 pairs
+        qk.qk_gram_pairs_noalloc(small, small, dp.to(torch.int64), out)
+    with pytest.raises(ValueError):  # pairs not of shape (P, 2)
+        qk.qk_gram_pairs_noalloc(small, small, torch.zeros(2, dtype=torch.int32, device="cuda"), out)
+
+
+def test_noalloc_allocates_no_device_memory(qk):
+    """After a first call on the device, further calls leave the device's
+    free memory and torch's caching allocator untouched."""
+    import torch
+    st = states(6, 11, 8, (8, 16))
+    A = qk.qk_mps_import(st, store="c64")
+    pairs = torch.tensor([[i, j] for i in range(6) for j in range(6)], dtype=torch.int32, device="cuda")
+    out = torch.empty(len(pairs), dtype=torch.float64, device="cuda")
+    qk.qk_gram_pairs_noalloc(A, A, pairs, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    qk.qk_gram_pairs_noalloc(A, A, pairs, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for key in ("allocated_bytes.all.current", "reserved_bytes.all.current", "allocation.all.allocated"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
