@@ -4,19 +4,19 @@
 Workload (the n=165 circuit of the headline metric): n=165 qubits/features,
 interaction distance d=6, r=2 repetitions, gamma=0.15, chi_max=128,
 truncation eps=1e-8, complex64 states; synthetic stand-in for the Elliptic
-data (standardised correlated Gaussian features, 6400 training rows).
+data (standardised correlated Gaussian features, 6400 training rows).  Each
+rank takes `--n-states` distinct training rows of its own.
 
-Setup (untimed): each rank builds `--distinct` states from its own training
-rows with the FP64 builder, then expands them to `--n-states` distinct
-states by a final random Rz layer per copy (single-qubit Z rotations
-contracted into the sites: bond profiles unchanged, overlaps between copies
-as small as between different data points).
+End to end (also the setup, timed once): pinned host X -> qk_build_states
+(FP64 builder) -> qk_gram (split precision) -> pinned host K.
 
-Step (timed): one qk_gram call on the resident batch - the symmetric Gram
-(i <= j contracted and mirrored) by the split-precision tensor-core sweep,
-with FP64 re-evaluation of the entries above 1e-3 (the diagonal).  value =
-computed entries (N(N+1)/2 per rank, summed over ranks) / max-over-ranks time.
-Inputs (the packed states, GBs) are far larger than L2.
+Step (timed, inputs resident in HBM): one qk_gram call on the built batch -
+the symmetric Gram (i <= j contracted and mirrored) by the split-precision
+tensor-core sweep, with FP64 re-evaluation of the entries above 1e-3 (the
+refinement floor is 0 in the headline; the configured floor 1e-4 is timed
+separately on a subset, where it sends nearly every entry to FP64).  value =
+computed entries (N(N+1)/2 per rank, summed over ranks) / max-over-ranks
+time.  Inputs (the packed states, GBs) are far larger than L2.
 
 --impl reference times the CPU oracle (numpy, FP64) on a bounded sample of
 the same workload on the host cores.
@@ -39,23 +39,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gram entries/s (n=165, chi=128), split-precision vs FP64 path on 1 GB300 at |dK|<=1e-5"
 
+# The tile schedule the benchmark pins (one ket per tile, bands of 128
+# bras), so that the ncu figures in profiles/ describe the launch it times.
+BENCH_SCHEDULE = {"kets_per_tile": 1, "band": 128}
+
 # DRAM bytes (read + write) per off-diagonal pair of tc_overlap_kernel<2> at
-# the n=165, d=6, chi_max=128 circuit, from one ncu capture of a 192-state
-# symmetric Gram (18,336 pairs, 568.2 GB in one launch).  The roofline's
-# `traffic` scales it to the pairs of one launch; it holds only for that
-# kernel version, the split depth P=2 and the tile schedule it was taken
-# with (4 kets per tile, bands of 16 bras); another schedule reports null.
-TC_DRAM_BYTES_PER_PAIR = 568.189336e9 / 18336
-TC_TRAFFIC_SCHEDULE = {"kets_per_tile": 4, "band": 16}
+# the n=165, d=6, chi_max=128 circuit with BENCH_SCHEDULE, from one ncu
+# capture of a smaller symmetric Gram of the same circuit (the capture's
+# dram__bytes_read.sum + dram__bytes_write.sum divided by its pairs; see
+# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 235.36 GB for the
+# 11,476 pairs of a 152-state Gram).  Per-pair time is the same at 152 and
+# 1216 states, so the per-pair traffic is taken as independent of N.
+TC_DRAM_BYTES_PER_PAIR = 235.358644e9 / 11476
 
 
 def roofline_traffic(prec, schedule, pairs):
     """DRAM bytes of one tensor-core launch over `pairs` pairs, from the ncu
     per-pair figure; None unless the run used the captured depth and tile
     schedule."""
-    if prec != "split" or not schedule:
+    if prec != "split" or not schedule or TC_DRAM_BYTES_PER_PAIR is None:
         return None
-    if any(schedule.get(k) != v for k, v in TC_TRAFFIC_SCHEDULE.items()):
+    if any(schedule.get(k) != v for k, v in BENCH_SCHEDULE.items()):
         return None
     return TC_DRAM_BYTES_PER_PAIR * pairs
 
@@ -66,12 +70,12 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n-states", type=int, default=1824)
-    p.add_argument("--distinct", type=int, default=152)
+    p.add_argument("--n-states", type=int, default=1216, help="distinct c165 states per rank")
+    p.add_argument("--subset", type=int, default=152, help="states of the FP64-path and floor-1e-4 legs")
     p.add_argument("--prec", default="split", choices=["split", "split_bf16x3", "fp64"])
-    p.add_argument("--fp64-sample", type=int, default=1, help="0 skips the FP64-path comparison")
+    p.add_argument("--check-pairs", type=int, default=2048, help="sampled FP64 check of the timed Gram")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the subset, load-only and inference legs")
     return p.parse_args()
 
 
@@ -103,22 +107,48 @@ def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
 
 
 # --------------------------------------------------------------------- helpers
-def gram_flops(dims: np.ndarray, diagonal: bool = False) -> float:
-    """Algorithmic real FLOPs of the pairs (bra i, ket j), i < j (and i = j
-    when `diagonal`): per pair and site, T_s = E B[s] then
-    E' = sum_s A[s]^H T_s, i.e. 2 (chi^a_k chi^b_k chi^b_k+1 +
-    chi^a_k+1 chi^a_k chi^b_k+1) complex MACs, 8 real FLOPs each.  The count
-    is not symmetric in (i, j), so it is summed in order with prefix sums."""
+def gram_flops(dims: np.ndarray, diagonal: bool = False, order: str = "kernel") -> float:
+    """Real FLOPs of the transfer sweeps of the pairs (bra i, ket j), i < j
+    (and i = j when `diagonal`); 8 real FLOPs per complex MAC.  Per pair and
+    site the two half-steps cost
+      (a) T_s = E B[s], E' = sum_s A[s]^H T_s:
+          2 chi^a_k chi^b_k chi^b_k+1 + 2 chi^a_k+1 chi^a_k chi^b_k+1 MACs,
+      (b) F_s = A[s]^H E, E' = sum_s F_s B[s]:
+          2 chi^a_k+1 chi^a_k chi^b_k + 2 chi^a_k+1 chi^b_k chi^b_k+1 MACs.
+    order="kernel" counts (a), the order the tensor-core kernel uses;
+    order="min" takes the cheaper of (a) and (b) per pair and site (the
+    algorithmic work of the method)."""
     c = dims.astype(np.float64)
     c0, c1 = c[:, :-1], c[:, 1:]
-    bra1, ket1 = c0, c0 * c1          # chi^a_k      * (chi^b_k chi^b_k+1)
-    bra2, ket2 = c1 * c0, c1          # chi^a_k+1 chi^a_k * chi^b_k+1
-    pre1 = np.cumsum(bra1, axis=0) - bra1  # sum over i < j
-    pre2 = np.cumsum(bra2, axis=0) - bra2
-    total = np.sum(ket1 * pre1) + np.sum(ket2 * pre2)
-    if diagonal:
-        total += np.sum(bra1 * ket1 + bra2 * ket2)
+    N = c.shape[0]
+    if order == "kernel":
+        bra1, ket1 = c0, c0 * c1          # chi^a_k      * (chi^b_k chi^b_k+1)
+        bra2, ket2 = c1 * c0, c1          # chi^a_k+1 chi^a_k * chi^b_k+1
+        pre1 = np.cumsum(bra1, axis=0) - bra1  # sum over i < j
+        pre2 = np.cumsum(bra2, axis=0) - bra2
+        total = np.sum(ket1 * pre1) + np.sum(ket2 * pre2)
+        if diagonal:
+            total += np.sum(bra1 * ket1 + bra2 * ket2)
+        return 16.0 * total
+    total = 0.0
+    for i in range(N):  # bra i against the kets j > i (j >= i with the diagonal)
+        j0 = i if diagonal else i + 1
+        if j0 >= N:
+            continue
+        a0, a1 = c0[i][None, :], c1[i][None, :]
+        b0, b1 = c0[j0:], c1[j0:]
+        ca = a0 * b0 * b1 + a1 * a0 * b1
+        cb = a1 * a0 * b0 + a1 * b0 * b1
+        total += np.sum(np.minimum(ca, cb))
     return 16.0 * total
+
+
+FP64_DFMA_PER_CLK_PER_SM = 2  # GB300: 1.25 TFLOP/s FP64 at 152 SMs x 2.07 GHz
+
+
+def fp64_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """FP64 ALU peak from the unit count and the SM clock seen under load."""
+    return 2.0 * FP64_DFMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -280,6 +310,7 @@ def run_ours(a):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -287,32 +318,43 @@ def run_ours(a):
     import workloads
 
     w = workloads.c165()
-    rows = rank_rows(w.X_train, rank, a.distinct)
-    stream = torch.cuda.current_stream()
+    rows = rank_rows(w.X_train, rank, a.n_states)
+    N = len(rows)
+    entries = N * (N + 1) // 2
+    prec = a.prec
 
-    # ---- setup: FP64 builder, then rotated copies
+    # ---- end to end through the public API (also the setup): pinned host X
+    # -> build -> Gram -> pinned host K, timed once
+    Xh = torch.from_numpy(np.ascontiguousarray(rows)).pin_memory()
+    Kh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.time()
-    base = qk.qk_build_states(rows, w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+    A = qk.qk_build_states(Xh, w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+    t_build = time.time() - t0
+    bprof = qk.qk_last_build_profile()
+    if prec != "fp64":
+        qk.qk_set_split_schedule(A, prec=prec, **BENCH_SCHEDULE)
+    qk.qk_gram(A, prec=prec, out=Kh)
     torch.cuda.synchronize()
-    build_s = time.time() - t0
-    copies = max(1, a.n_states // a.distinct)
-    rng = np.random.default_rng(1000 + rank)
-    phi = rng.uniform(-math.pi, math.pi, size=(copies, w.n))
-    phi[0] = 0.0  # copy 0 is the built states themselves
-    A = qk.qk_mps_rz_copies(base, phi)
-    N = A.N
+    t_e2e = time.time() - t0
+    e2e_s = max_over_ranks(1000.0 * t_e2e, world) / 1000.0
+    e2e = {"value": entries * world / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": int(Xh.numel() * 8),
+           "d2h_bytes_per_step": int(N * N * 8), "steps": 1,
+           "path": "pinned host X -> qk_build_states -> qk_gram -> pinned host K",
+           "build_s": round(t_build, 2), "gram_s": round(t_e2e - t_build, 3)}
     dims = A.bond_dims()
-    flops = gram_flops(dims)
+    flops = gram_flops(dims, order="min")
+    flops_kernel = gram_flops(dims, order="kernel")
+    stream = torch.cuda.current_stream()
+    Kbuf = torch.empty((N, N), dtype=torch.float64, device="cuda")
 
     def step():
-        K, nref = qk.qk_gram(A, prec=a.prec, out=Kbuf)
+        _, nref = qk.qk_gram(A, prec=prec, out=Kbuf)
         return nref
 
-    Kbuf = torch.empty((N, N), dtype=torch.float64, device="cuda")
     for _ in range(a.warmup):
-        step()  # the first split call also tunes the tile schedule
-    schedule = qk.qk_tune_split(A, prec=a.prec) if a.prec != "fp64" else None
+        step()
+    schedule = qk.qk_tune_split(A, prec=prec) if prec != "fp64" else None
     # ---- timed region
     sampler = ClockSampler(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,88 +374,141 @@ def run_ours(a):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    entries = N * (N + 1) // 2
     value = entries * world * a.steps / (ms / 1000.0)
 
-    # ---- FP64 path on the same GPU, on the built (distinct) states
-    fp64 = None
-    if a.prec != "fp64" and a.fp64_sample > 0:
-        sub = base
-        Ks, _ = qk.qk_gram(sub, prec=a.prec)
+    # ---- sampled FP64 check of the Gram that was timed (off-diagonal pairs)
+    check = None
+    if a.check_pairs > 0 and N > 1:
+        rng = np.random.default_rng(77 + rank)
+        i = rng.integers(0, N, a.check_pairs)
+        j = rng.integers(0, N, a.check_pairs)
+        keep = i != j
+        pairs = np.stack([np.minimum(i, j), np.maximum(i, j)], axis=1)[keep].astype(np.int32)
+        k64 = qk.qk_gram_pairs(A, A, pairs, prec="fp64").cpu().numpy()
+        kt = Kbuf.cpu().numpy()[pairs[:, 0], pairs[:, 1]]
+        check = {"pairs": int(len(pairs)), "max_abs_dK_vs_fp64": float(np.max(np.abs(kt - k64))),
+                 "max_K": float(np.max(k64)), "median_K": float(np.median(k64))}
+
+    extra = {}
+    if not a.no_extra and prec != "fp64":
+        # ---- FP64 path, and the configured refinement floor 1e-4, on a subset
+        sub_n = min(a.subset, N)
+        sub = qk.qk_build_states(Xh[:sub_n], w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+        e_sub = sub_n * (sub_n + 1) // 2
+        Ks, _ = qk.qk_gram(sub, prec=prec)
         torch.cuda.synchronize()
         t0 = time.time()
         K64, _ = qk.qk_gram(sub, prec="fp64")
         torch.cuda.synchronize()
-        dt = time.time() - t0
-        e64 = sub.N * (sub.N + 1) // 2
-        fp64 = {"value": e64 / dt, "unit": "entries/s", "states": sub.N,
-                "max_abs_dK_split_vs_fp64": float((Ks - K64).abs().max().item())}
-
-    # ---- end to end through the public API with host buffers
-    e2e = None
-    if not a.no_e2e:
+        dt64 = time.time() - t0
+        t0 = time.time()
+        Kf, nref_f = qk.qk_gram(sub, prec=prec, refine_floor=1e-4)
+        torch.cuda.synchronize()
+        dtf = time.time() - t0
+        t0 = time.time()
+        qk.qk_gram(sub, prec=prec)
+        torch.cuda.synchronize()
+        dts = time.time() - t0
+        extra["fp64_path"] = {"value": e_sub / dt64, "unit": "entries/s", "states": sub_n,
+                              "max_abs_dK_split_vs_fp64": float((Ks - K64).abs().max().item())}
+        extra["split_floor_1e-4"] = {"value": e_sub / dtf, "unit": "entries/s", "states": sub_n,
+                                     "refined_fraction": nref_f / e_sub,
+                                     "max_abs_dK_vs_fp64": float((Kf - K64).abs().max().item())}
+        extra["split_floor_0_same_subset"] = {"value": e_sub / dts, "unit": "entries/s", "states": sub_n}
+        sub.free()
+        # ---- end to end from a host blob (load + Gram), without the build
         nb = qk.qk_mps_blob_bytes(A)
         blob = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
         qk.qk_mps_save(A, blob)
-        Kh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
         t0 = time.time()
-        for _ in range(a.steps):
-            # a fresh batch per step: the tile schedule tuned above is found
-            # again by the Gram's shape, not re-timed
+        reps = 2
+        for _ in range(reps):
             B = qk.qk_mps_load(blob)
-            qk.qk_gram(B, prec=a.prec, out=Kh)
+            qk.qk_gram(B, prec=prec, out=Kh)
             B.free()
         torch.cuda.synchronize()
-        dt = max_over_ranks(1000.0 * (time.time() - t0), world) / 1000.0
-        e2e = {"value": entries * world * a.steps / dt, "unit": "entries/s", "h2d_bytes_per_step": int(nb),
-               "d2h_bytes_per_step": int(N * N * 8), "steps": a.steps}
+        dt = time.time() - t0
+        extra["e2e_load"] = {"value": entries * reps / dt, "unit": "entries/s", "h2d_bytes_per_step": int(nb),
+                             "d2h_bytes_per_step": int(N * N * 8), "steps": reps,
+                             "path": "pinned host blob -> qk_mps_load -> qk_gram -> pinned host K"}
+        del blob
+        # ---- single-point inference: build one test state, then its row of K
+        xt = torch.from_numpy(np.ascontiguousarray(w.X_test[rank:rank + 1])).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        T1 = qk.qk_build_states(xt, w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+        t1 = time.time()
+        row = torch.empty((1, N), dtype=torch.float64, pin_memory=True)
+        qk.qk_gram(T1, A, prec=prec, out=row)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        extra["inference_one_point"] = {"build_s": round(t1 - t0, 3), "row_s": round(t2 - t1, 4),
+                                        "total_s": round(t2 - t0, 3), "train_states": N}
+        T1.free()
 
     # kernels of one split qk_gram on a symmetric batch: the tensor-core sweep,
     # the self-overlaps, the refinement selection, and, when entries were
     # selected, the FP64 sweep over them and their scatter into K
-    if a.prec == "fp64":
+    if prec == "fp64":
         launches = a.steps
     else:
         launches = sum(3 + (2 if r > N else 0) for r in nrefs)
-    pairs = N * (N - 1) // 2
-    traffic = roofline_traffic(a.prec, schedule, pairs)
+    pairs_n = N * (N - 1) // 2
+    traffic = roofline_traffic(prec, schedule, pairs_n)
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     kavg = float(np.mean(kern_ms)) if kern_ms else float("nan")
     achieved = flops / (kavg / 1000.0) / 1e12
+    sm_mhz = clocks.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    b_ms = bprof["kernel_ms"]
+    b_tflops = bprof["fp64_flops"] / (b_ms / 1000.0) / 1e12 if b_ms > 0 else None
+    b_peak = fp64_peak_tflops(sm_mhz, sms)
+    store_bytes = A.nbytes()
     out = {
         "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x2-split->f32" if a.prec == "split" else
-        ("bf16x3-split->f32" if a.prec == "split_bf16x3" else "f64"),
+        "vs_baseline": None, "dtype": "bf16x2-split->f32" if prec == "split" else
+        ("bf16x3-split->f32" if prec == "split_bf16x3" else "f64"),
         "data": "synthetic",
-        "config": {"workload": "c165: n=165 d=6 r=2 gamma=0.15 chi_max=128 eps=1e-8, complex64 states",
-                   "states_per_rank": N, "distinct_built_per_rank": a.distinct,
-                   "expansion": f"{copies} copies per built state via a random final Rz layer",
-                   "gram": "symmetric, i<=j contracted, FP64 re-evaluation above 1e-3",
-                   "prec": a.prec, "l2": "inputs larger than L2 (packed states GBs)",
+        "config": {"workload": f"c165: n=165 d=6 r=2 gamma=0.15 chi_max=128 eps=1e-8, {N} distinct built "
+                               f"states per rank (complex64)",
+                   "states_per_rank": N,
+                   "gram": "symmetric, i<=j contracted, FP64 re-evaluation above 1e-3, refinement floor 0",
+                   "prec": prec, "l2": "inputs larger than L2 (packed states GBs)",
                    "mean_chi": float(dims.mean()), "max_chi": int(dims.max()),
                    "tile_schedule": schedule},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "tc_overlap_kernel", "peak_source": f"bf16_tflops_sustained ({src})",
                      "algorithmic_tflop_per_launch": flops / 1e12,
+                     "kernel_order_tflop_per_launch": flops_kernel / 1e12,
                      "kernel_ms_per_launch": kavg, "refine_ms_per_step": float(np.mean(refine_ms)),
-                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a 192-state "
-                                        "capture, per pair, times the launch's pairs") if traffic else
-                                       ("null: the ncu capture was taken with the schedule "
-                                        f"{TC_TRAFFIC_SCHEDULE}, this run used {schedule}"),
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a 152-state capture "
+                                        "with the same schedule, per pair, times the launch's pairs") if traffic
+                                       else "null: no ncu capture of this kernel version with this schedule",
                      "dram_tb_per_s": (traffic / (kavg / 1000.0) / 1e12) if traffic else None,
-                     "note": "algorithmic complex-MAC FLOPs; the bf16x2 split issues 3 bf16 products per "
-                             "real product, so frac <= 1/3 at full tensor-pipe use"},
+                     "note": "algorithmic = cheaper contraction order per pair and site (complex MACs x 8); "
+                             "the kernel issues the fixed order (kernel_order_tflop_per_launch) as 3 bf16 "
+                             "products per real product, so frac <= 1/3 at full tensor-pipe use"},
+        "builder": {"states": N, "seconds": round(t_build, 2), "states_per_s": N / t_build,
+                    "kernel_ms": b_ms, "ctas": bprof["ctas"],
+                    "sweeps_per_factorisation": bprof["sweeps"] / max(1, bprof["factorisations"]),
+                    "phase_share": {k: v / max(1e-9, sum(bprof["phase_sm_ms"].values()))
+                                    for k, v in bprof["phase_sm_ms"].items()},
+                    "roofline": {"bound": "alu", "achieved": b_tflops, "peak": b_peak, "unit": "TFLOP/s",
+                                 "frac": (b_tflops / b_peak) if b_tflops else None,
+                                 "peak_source": "FP64: 2 DFMA/clk/SM x SMs x median SM clock",
+                                 "fp64_tflop": bprof["fp64_flops"] / 1e12,
+                                 "hbm_gbs": (store_bytes + Xh.numel() * 8) / (b_ms / 1000.0) / 1e9,
+                                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}},
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": e2e,
-        "fp64_path": fp64,
-        "builder": {"states": base.N, "seconds": round(build_s, 1), "states_per_s": base.N / build_s},
+        "timed_gram_check": check,
         "n_refined_per_step": int(np.mean(nrefs)) if nrefs else 0,
     }
+    out.update(extra)
     if rank == 0 and not a.no_cpu_baseline:
         v, sample = cpu_oracle_rate()
         out["cpu_baseline"] = {"value": v, "unit": "entries/s", "cores": sample["procs"], "kind": "oracle",

@@ -114,11 +114,14 @@ qk_status qk_build_states(const double* X, int64_t N, int32_t n, int32_t d,
  *                   the factors (isometry + GEMM), centre moves, other (Z
  *                   layers, packing);
  *   ctas            CTAs launched; sweeps  Jacobi sweeps summed over all
- *                   factorisations; factorisations  their number.
+ *                   factorisations; factorisations  their number;
+ *   fp64_flops      FP64 flops the kernel executed (an FMA counts 2): theta
+ *                   formation and gate, QR updates, Jacobi inner products and
+ *                   rotations, the GEMMs that form the factors.
  * Any pointer may be NULL.  No synchronisation. */
 qk_status qk_last_build_profile(double* kernel_ms, double* phase_sm_ms,
                                 int64_t* ctas, int64_t* sweeps,
-                                int64_t* factorisations);
+                                int64_t* factorisations, double* fp64_flops);
 
 /* Number of two-site ops in one repetition: sum_i (2 min(d, n-1-i) - 1). */
 int64_t qk_schedule_length(int32_t n, int32_t d);

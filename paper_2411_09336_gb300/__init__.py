@@ -59,7 +59,8 @@ _sig("qk_mps_blob_bytes", [_vp, C.POINTER(_i64)])
 _sig("qk_mps_save", [_vp, _vp, _i64])
 _sig("qk_mps_load", [_vp, _i64, _vp, C.POINTER(_vp)])
 _sig("qk_last_profile", [C.POINTER(_f64), C.POINTER(_f64), C.POINTER(_f64)])
-_sig("qk_last_build_profile", [C.POINTER(_f64), _vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)])
+_sig("qk_last_build_profile", [C.POINTER(_f64), _vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
+                               C.POINTER(_f64)])
 _sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
 _sig("qk_debug_stall_next_split", [_i32])
 _sig("qk_tune_split", [_vp, _vp, C.c_int, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_f64)])
@@ -308,11 +309,11 @@ def qk_last_build_profile() -> dict:
     factorisations."""
     ms = _f64()
     ph = np.zeros(len(BUILD_PHASES), dtype=np.float64)
-    ctas, sw, nf = _i64(), _i64(), _i64()
-    _check(_lib.qk_last_build_profile(C.byref(ms), ph.ctypes.data, C.byref(ctas), C.byref(sw), C.byref(nf)),
-           "qk_last_build_profile")
+    ctas, sw, nf, fl = _i64(), _i64(), _i64(), _f64()
+    _check(_lib.qk_last_build_profile(C.byref(ms), ph.ctypes.data, C.byref(ctas), C.byref(sw), C.byref(nf),
+                                      C.byref(fl)), "qk_last_build_profile")
     return {"kernel_ms": ms.value, "phase_sm_ms": dict(zip(BUILD_PHASES, ph.tolist())), "ctas": ctas.value,
-            "sweeps": sw.value, "factorisations": nf.value}
+            "sweeps": sw.value, "factorisations": nf.value, "fp64_flops": fl.value}
 
 
 def qk_gram_pairs_noalloc(A: MPSBatch, B: MPSBatch, pairs, out, stream=None):

@@ -57,7 +57,7 @@ constexpr int kMaxSweeps = 60;
 constexpr int kMaxCols = 256;   // 2 * chi_max
 constexpr int kMaxN = 1024;     // qubits
 #ifndef QK_BUILD_CTAS
-#define QK_BUILD_CTAS 1
+#define QK_BUILD_CTAS 2
 #endif
 constexpr int kCtas = QK_BUILD_CTAS;  // CTAs per SM
 // complex doubles of the shared-memory copy of Y; larger Y live in HBM/L2
@@ -66,7 +66,7 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr unsigned kFull = 0xffffffffu;
 
 // per-CTA profile counters (clock64 cycles per phase, counts)
-enum Prof { PF_THETA = 0, PF_QR, PF_JACOBI, PF_OUT, PF_MOVE, PF_OTHER, PF_SWEEPS, PF_FACTOR, PF_N };
+enum Prof { PF_THETA = 0, PF_QR, PF_JACOBI, PF_OUT, PF_MOVE, PF_OTHER, PF_SWEEPS, PF_FACTOR, PF_FLOPS, PF_N };
 
 struct BuildArgs {
   const double* X;         // [N][n]
@@ -132,6 +132,7 @@ struct Shared {
   int bad;
   int need;                 // kept columns to be completed
   int sweeps;
+  unsigned long long flops; // FP64 flops executed (FMA = 2), flushed per state
 };
 
 struct Work {
@@ -160,6 +161,7 @@ __device__ __forceinline__ void prof_add(const Work& w, int what, unsigned long 
 __device__ void qrcp(double2* Y, int n, int m, Shared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = min(n, m);
+  if (tid == 0) sh.flops += 4ull * n * m;
   for (int c = tid; c < m; c += kThreads) {
     double s = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -252,6 +254,7 @@ __device__ void qrcp(double2* Y, int n, int m, Shared& sh) {
     const double hinv = sh.hinv;
     if (hinv == 0.0) break;
     const int nc = m - j - 1, nr = n - j;
+    if (tid == 0) sh.flops += 20ull * nr * (nc > 0 ? nc : 0) + 8ull * nr;
     if (nc > 0) {
       int G = 1;  // lanes per column
       while (G < 32 && 2 * G * nc <= kThreads && G < nr) G <<= 1;
@@ -318,7 +321,10 @@ __device__ bool jacobi_rows(double2* Y, int kq, int m, double kappa, Shared& sh)
       s = warp_sum(s);
       if (lane == 0) sh.nrm[j] = s;
     }
-    if (tid == 0) sh.rotated = 0;
+    if (tid == 0) {
+      sh.rotated = 0;
+      sh.flops += 4ull * kq * m;
+    }
     __syncthreads();
     for (int round = 0; round < npad - 1; ++round) {
       for (int k0 = 0; k0 < npairs; k0 += per) {
@@ -350,6 +356,7 @@ __device__ bool jacobi_rows(double2* Y, int kq, int m, double kappa, Shared& sh)
         int rot = 0;
         double c = 1.0, sx = 0.0, sy = 0.0;
         if (valid && tl == 0) {
+          atomicAdd(&sh.flops, 8ull * m);  // w_p^H w_q
           const double a = sh.nrm[p], b = sh.nrm[q];
           const double g = sqrt(gr * gr + gi * gi);
           if (a > 0.0 && b > 0.0 && g > 0.0) {
@@ -371,6 +378,7 @@ __device__ bool jacobi_rows(double2* Y, int kq, int m, double kappa, Shared& sh)
                 sh.nrm[p] = fmax(a - t * g, 0.0);
                 sh.nrm[q] = b + t * g;
                 atomicAdd(&sh.rotated, 1);
+                atomicAdd(&sh.flops, 20ull * m);  // the rotation of both rows
               }
             }
           }
@@ -609,7 +617,10 @@ __device__ void move_right(const BuildArgs& a, Work& w, int c, Shared& sh, unsig
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * k * cn; i += kThreads) An[i] = w.T0[i];
-  if (threadIdx.x == 0) sh.chi[c + 1] = k;
+  if (threadIdx.x == 0) {
+    sh.chi[c + 1] = k;
+    sh.flops += 8ull * k * m * n + 16ull * k * cn * cr;
+  }
   __syncthreads();
   prof_add(w, PF_MOVE, t0);
 }
@@ -669,7 +680,10 @@ __device__ void move_left(const BuildArgs& a, Work& w, int c, Shared& sh, unsign
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * cp * k; i += kThreads) Ap[i] = w.T0[i];
-  if (threadIdx.x == 0) sh.chi[c] = k;
+  if (threadIdx.x == 0) {
+    sh.chi[c] = k;
+    sh.flops += 8ull * cl * k * ncol + 16ull * cp * k * cl;
+  }
   __syncthreads();
   prof_add(w, PF_MOVE, t0);
 }
@@ -721,6 +735,7 @@ __device__ void two_site(const BuildArgs& a, Work& w, const double* x, const Op 
     else
       Y[i] = th;
   }
+  if (threadIdx.x == 0) sh.flops += 8ull * rows * cols * cm + 6ull * rows * cols;
   __syncthreads();
   prof_add(w, PF_THETA, t0);
   factor(w, Y, n, m, a.eps, sh, t0);
@@ -776,7 +791,10 @@ __device__ void two_site(const BuildArgs& a, Work& w, const double* x, const Op 
       Ap[((int64_t)(row & 1) * cl + (row >> 1)) * r + j] = make_double2(acc.x * nrm, acc.y * nrm);
     }
   }
-  if (threadIdx.x == 0) sh.chi[p + 1] = r;
+  if (threadIdx.x == 0) {
+    sh.chi[p + 1] = r;
+    sh.flops += 8ull * r * rows * cols;
+  }
   __syncthreads();
   prof_add(w, PF_OUT, t0);
 }
@@ -793,7 +811,10 @@ __global__ void __launch_bounds__(kThreads, kCtas) build_kernel(BuildArgs a) {
   w.prof = a.prof ? a.prof + (int64_t)blockIdx.x * PF_N : nullptr;
   unsigned long long t0 = clock64();
   const int n = a.n;
-  if (threadIdx.x == 0) sh.sweeps = 0;
+  if (threadIdx.x == 0) {
+    sh.sweeps = 0;
+    sh.flops = 0ull;
+  }
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) sh.sample = atomicAdd(a.queue, 1);
@@ -895,7 +916,10 @@ __global__ void __launch_bounds__(kThreads, kCtas) build_kernel(BuildArgs a) {
     }
     prof_add(w, PF_OTHER, t0);
   }
-  if (w.prof && threadIdx.x == 0) w.prof[PF_SWEEPS] += sh.sweeps;
+  if (w.prof && threadIdx.x == 0) {
+    w.prof[PF_SWEEPS] += sh.sweeps;
+    w.prof[PF_FLOPS] += sh.flops;
+  }
 }
 
 // profile of the last qk_build_states call on this thread
@@ -903,6 +927,7 @@ struct BuildProfile {
   double kernel_ms = 0.0;
   double sm_ms[PF_OTHER + 1] = {};  // per phase, SM-milliseconds summed over CTAs
   int64_t ctas = 0, sweeps = 0, factors = 0;
+  double flops = 0.0;  // FP64 flops executed
 };
 thread_local BuildProfile g_bprof;
 
@@ -1096,6 +1121,7 @@ qk_status build_states_device(const double* dX, int64_t N, int n, int d, int rep
       for (int f = PF_THETA; f <= PF_OTHER; ++f) bp.sm_ms[f] += (double)row[f] / (double)clock_khz;
       bp.sweeps += (int64_t)row[PF_SWEEPS];
       bp.factors += (int64_t)row[PF_FACTOR];
+      bp.flops += (double)row[PF_FLOPS];
     }
     g_bprof = bp;
   }
@@ -1108,8 +1134,9 @@ qk_status build_states_device(const double* dX, int64_t N, int n, int d, int rep
 }  // namespace qk
 
 extern "C" qk_status qk_last_build_profile(double* kernel_ms, double* phase_sm_ms, int64_t* ctas,
-                                          int64_t* sweeps, int64_t* factorisations) {
+                                          int64_t* sweeps, int64_t* factorisations, double* fp64_flops) {
   const qk::BuildProfile& b = qk::g_bprof;
+  if (fp64_flops) *fp64_flops = b.flops;
   if (kernel_ms) *kernel_ms = b.kernel_ms;
   if (phase_sm_ms)
     for (int f = 0; f <= qk::PF_OTHER; ++f) phase_sm_ms[f] = b.sm_ms[f];

@@ -28,6 +28,31 @@ def test_gram_flops_brute_force():
     assert bench.gram_flops(dims, diagonal=True) == pytest.approx(strict + diag, rel=1e-12)
 
 
+def test_gram_flops_min_order_brute_force():
+    """The algorithmic count takes, per pair and site, the cheaper of the two
+    contraction orders (E B first, or A^H E first)."""
+    rng = np.random.default_rng(1)
+    N, n = 6, 8
+    dims = np.ones((N, n + 1), dtype=np.int64)
+    dims[:, 1:-1] = rng.integers(1, 50, size=(N, n - 1))
+    strict = 0.0
+    for i in range(N):
+        for j in range(i + 1, N):
+            a, b = dims[i], dims[j]
+            for k in range(n):
+                ca = a[k] * b[k] * b[k + 1] + a[k + 1] * a[k] * b[k + 1]
+                cb = a[k + 1] * a[k] * b[k] + a[k + 1] * b[k] * b[k + 1]
+                strict += 16.0 * min(ca, cb)
+    got = bench.gram_flops(dims, order="min")
+    assert got == pytest.approx(strict, rel=1e-12)
+    assert got <= bench.gram_flops(dims)
+
+
+def test_fp64_peak_from_unit_count():
+    # 2 DFMA per clock per SM at 152 SMs and 2070 MHz: the nominal 1.25 TFLOP/s
+    assert bench.fp64_peak_tflops(2070.0, 152) == pytest.approx(1.2586, rel=1e-3)
+
+
 def test_rank_rows_disjoint_and_checked():
     X = np.arange(40 * 3, dtype=float).reshape(40, 3)
     blocks = [bench.rank_rows(X, r, 8) for r in range(5)]
@@ -74,10 +99,13 @@ def test_two_gloo_ranks():
     assert set(res[0][2]).isdisjoint(res[1][2])
 
 
-def test_roofline_traffic_only_for_the_captured_schedule():
-    sch = dict(bench.TC_TRAFFIC_SCHEDULE)
-    assert bench.roofline_traffic("split", sch, 10) == bench.TC_DRAM_BYTES_PER_PAIR * 10
-    assert bench.roofline_traffic("split", {**sch, "kets_per_tile": 1}, 10) is None
+def test_roofline_traffic_only_for_the_captured_schedule(monkeypatch):
+    sch = dict(bench.BENCH_SCHEDULE)
+    monkeypatch.setattr(bench, "TC_DRAM_BYTES_PER_PAIR", 1.5e6)
+    assert bench.roofline_traffic("split", sch, 10) == 1.5e7
+    assert bench.roofline_traffic("split", {**sch, "kets_per_tile": 4}, 10) is None
     assert bench.roofline_traffic("split_bf16x3", sch, 10) is None
     assert bench.roofline_traffic("fp64", None, 10) is None
     assert bench.roofline_traffic("split", {**sch, "us_per_pair": 7.0}, 10) is not None
+    monkeypatch.setattr(bench, "TC_DRAM_BYTES_PER_PAIR", None)
+    assert bench.roofline_traffic("split", sch, 10) is None
