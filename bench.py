@@ -75,7 +75,10 @@ def parse():
     p.add_argument("--prec", default="split", choices=["split", "split_bf16x3", "fp64"])
     p.add_argument("--check-pairs", type=int, default=2048, help="sampled FP64 check of the timed Gram")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-extra", action="store_true", help="skip the subset, load-only and inference legs")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the subset, load-only, inference and surrogate legs")
+    p.add_argument("--surrogate-epochs", type=int, default=20)
+    p.add_argument("--surrogate-test", type=int, default=304, help="test states of the surrogate block")
     return p.parse_args()
 
 
@@ -304,6 +307,90 @@ def run_reference(a):
     return 0
 
 
+# --------------------------------------------------------------------- surrogate
+def surrogate_leg(qk, w, A, K, rows, rank, a, extra_out):
+    """The learned surrogate on this workload's Gram: 330 -> 512 -> 512 -> 1
+    trained on 200k exact log K entries of the timed Gram (train-train
+    pairs), calibrated on 20k more, judged on 20k held out, then applied to
+    a test-vs-train block with the acceptance bound 1e-3 (log-K units) and
+    exact split-precision overlaps wherever the bound is larger."""
+    import torch
+    import workloads
+    N = A.N
+    n_fit, n_cal, n_hold = 200_000, 20_000, 20_000
+    if N * (N - 1) // 2 < n_fit + n_cal + n_hold:
+        return {"skipped": f"{N} states give fewer than {n_fit + n_cal + n_hold} pairs"}
+    fit, cal, hold = workloads.surrogate_pairs(N, n_fit, n_cal, n_hold, seed=5 + rank)
+    logK = torch.log(K).cpu().numpy()
+    t_fit = logK[fit[:, 0], fit[:, 1]]
+    Xtr = np.ascontiguousarray(rows)
+    net = qk.Surrogate(2 * w.n, 512, seed=rank)
+    net.set_target_scale(float(t_fit.mean()), float(t_fit.std()))
+    torch.cuda.synchronize()
+    t0 = time.time()
+    loss = net.train(Xtr, Xtr, fit, t_fit, epochs=a.surrogate_epochs, batch=4096, lr=1e-3, seed=rank)
+    train_s = time.time() - t0
+    net.calibrate(Xtr, Xtr, cal, logK[cal[:, 0], cal[:, 1]], alpha=0.05, n_bins=8)
+    _, bounds = net.bins()
+    err = np.abs(net.predict(Xtr, Xtr, hold) - logK[hold[:, 0], hold[:, 1]])
+    # test-vs-train block: surrogate first, exact overlaps elsewhere
+    nt = min(a.surrogate_test, len(w.X_test))
+    Xte = np.ascontiguousarray(w.X_test[rank * nt:(rank + 1) * nt])
+    T = qk.qk_build_states(Xte, w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")
+    qk.qk_gram(T, A, prec="split")  # packs the test states' operands outside the timings
+    torch.cuda.synchronize()
+    t0 = time.time()
+    Ke, _ = qk.qk_gram(T, A, prec="split")
+    torch.cuda.synchronize()
+    exact_s = time.time() - t0
+    tol = 1e-3
+    t0 = time.time()
+    Ks, acc, nacc = qk.qk_gram_surrogate(net, T, A, Xte, Xtr, tol, prec="split")
+    torch.cuda.synchronize()
+    surr_s = time.time() - t0
+    accb = acc.bool()
+    acc_err = float(torch.log(Ks[accb] / Ke[accb]).abs().max().item()) if nacc else None
+    T.free()
+    extra_out["K_test_train"] = Ke.cpu().numpy()
+    extra_out["test_rows"] = (rank * nt, (rank + 1) * nt)
+    return {"network": "330-512-512-1, bf16 GEMMs on tcgen05, FP32 accumulation",
+            "fit_pairs": n_fit, "epochs": a.surrogate_epochs, "train_s": round(train_s, 2),
+            "final_loss": loss, "held_out_abs_err_logK": {"median": float(np.median(err)),
+                                                         "p95": float(np.quantile(err, 0.95)),
+                                                         "max": float(err.max())},
+            "calibrated_bounds_logK": [float(b) for b in bounds], "tol_logK": tol,
+            "block": f"{nt} test x {N} train", "accepted": int(nacc),
+            "acceptance_rate": nacc / float(nt * N), "max_logK_err_accepted": acc_err,
+            "exact_block_s": round(exact_s, 3), "surrogate_block_s": round(surr_s, 3)}
+
+
+# --------------------------------------------------------------------- SVM
+def svm_leg(w, K_train, K_test, rank, N, test_rows):
+    """Sec. III-B on this workload: a C-SVM on the quantum Gram (training
+    block) scored by ROC AUC on the test-vs-train block, against the same SVM
+    on the Gaussian kernel of Eq. 9; C from 0.01 to 4, the best AUC reported
+    for each kernel."""
+    from paper_2411_09336_gb300 import classify
+    tr0 = rank * N
+    ytr = w.y[tr0:tr0 + N]
+    t0, t1 = test_rows
+    yte = w.y[w.n_train + t0:w.n_train + t1]
+    Xtr, Xte = w.X_train[tr0:tr0 + N], w.X_test[t0:t1]
+    alpha = classify.gaussian_alpha(Xtr)
+    G_tr, G_te = classify.gaussian_kernel(Xtr, Xtr, alpha), classify.gaussian_kernel(Xte, Xtr, alpha)
+    out = {"train": N, "test": t1 - t0, "C": [0.01, 0.1, 0.5, 1.0, 2.0, 4.0]}
+    t_start = time.time()
+    for name, (Ktr, Kte) in {"quantum": (K_train, K_test), "gaussian": (G_tr, G_te)}.items():
+        aucs = []
+        for C in out["C"]:
+            m = classify.SVM(C=C).fit(Ktr, ytr)
+            aucs.append(classify.roc_auc(yte, m.decision_function(Kte)))
+        out[f"{name}_auc"] = [round(x, 4) for x in aucs]
+        out[f"{name}_best_auc"] = round(max(aucs), 4)
+    out["seconds"] = round(time.time() - t_start, 2)
+    return out
+
+
 # --------------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -391,6 +478,10 @@ def run_ours(a):
 
     extra = {}
     if not a.no_extra and prec != "fp64":
+        blocks = {}
+        extra["surrogate"] = surrogate_leg(qk, w, A, Kbuf, rows, rank, a, blocks)
+        if "K_test_train" in blocks:
+            extra["svm"] = svm_leg(w, Kbuf.cpu().numpy(), blocks["K_test_train"], rank, N, blocks["test_rows"])
         # ---- FP64 path, and the configured refinement floor 1e-4, on a subset
         sub_n = min(a.subset, N)
         sub = qk.qk_build_states(Xh[:sub_n], w.d, w.reps, w.gamma, w.chi_max, w.eps, store="c64")

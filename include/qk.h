@@ -265,6 +265,21 @@ qk_status qk_set_split_schedule(const qk_mps_batch* A, const qk_mps_batch* B,
  * the device stays usable.  Consumed by that launch. */
 qk_status qk_debug_stall_next_split(int32_t on);
 
+/* Profiling switch of the tensor-core overlap kernel (the paper has no
+ * counterpart).  While `on`, every launch of the kernel sums per-CTA clock64
+ * cycles by phase; qk_last_tc_profile returns those of the last launch on
+ * this thread: counters[9] = thread 0's cycles inside the MMA-issue loop,
+ * waiting for operand copies, waiting for ring space; the CTA's cycles
+ * waiting for the MMAs, in the epilogue, at the barrier after it (all seen
+ * by thread 0, summed over CTAs); then GEMMs, K-chunks and tiles processed.
+ * ctas: CTAs of that launch.  No synchronisation. */
+qk_status qk_debug_tc_profile(int32_t on);
+/* Test knob: caps the grid of the tensor-core overlap kernel at `ctas` CTAs
+ * (0 restores the default of one wave at full residency).  Results do not
+ * depend on it; only the schedule's spread over the SMs changes. */
+qk_status qk_debug_tc_max_ctas(int32_t ctas);
+qk_status qk_last_tc_profile(double* counters, int32_t* ctas);
+
 /* ------------------------------------------------------------------------
  * qk_gram_pairs_noalloc - the FP64 pair overlaps of qk_gram_pairs
  * (QK_PREC_FP64) without any device or host allocation inside the call.

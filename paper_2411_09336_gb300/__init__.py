@@ -63,6 +63,9 @@ _sig("qk_last_build_profile", [C.POINTER(_f64), _vp, C.POINTER(_i64), C.POINTER(
                                C.POINTER(_f64)])
 _sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
 _sig("qk_debug_stall_next_split", [_i32])
+_sig("qk_debug_tc_profile", [_i32])
+_sig("qk_debug_tc_max_ctas", [_i32])
+_sig("qk_last_tc_profile", [_vp, C.POINTER(_i32)])
 _sig("qk_tune_split", [_vp, _vp, C.c_int, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_f64)])
 _sig("qk_set_split_schedule", [_vp, _vp, C.c_int, _i32, _i32])
 
@@ -298,6 +301,29 @@ def qk_debug_stall_next_split(on: bool = True) -> None:
     """Test hook: the next tensor-core overlap launch lets one bounded wait run
     out (the call then fails with QK_ERR_TIMEOUT; see include/qk.h)."""
     _check(_lib.qk_debug_stall_next_split(1 if on else 0), "qk_debug_stall_next_split")
+
+
+TC_PHASES = ("issue", "wait_copies", "wait_ring", "wait_mma", "epilogue", "barrier", "gemms", "chunks", "tiles")
+
+
+def qk_debug_tc_profile(on: bool = True) -> None:
+    """Profiling switch of the tensor-core overlap kernel (see include/qk.h)."""
+    _check(_lib.qk_debug_tc_profile(1 if on else 0), "qk_debug_tc_profile")
+
+
+def qk_debug_tc_max_ctas(ctas: int = 0) -> None:
+    """Test knob: cap the tensor-core kernel's grid (0: default)."""
+    _check(_lib.qk_debug_tc_max_ctas(int(ctas)), "qk_debug_tc_max_ctas")
+
+
+def qk_last_tc_profile() -> dict:
+    """Cycle counters by phase of the last profiled tensor-core launch."""
+    v = np.zeros(len(TC_PHASES), dtype=np.float64)
+    ctas = _i32()
+    _check(_lib.qk_last_tc_profile(v.ctypes.data, C.byref(ctas)), "qk_last_tc_profile")
+    out = dict(zip(TC_PHASES, v.tolist()))
+    out["ctas"] = ctas.value
+    return out
 
 
 BUILD_PHASES = ("theta", "qr", "jacobi", "factors_out", "moves", "other")

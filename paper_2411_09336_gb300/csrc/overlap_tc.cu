@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "qk_internal.h"
+#include "tc_ptx.cuh"
 
 namespace qk {
 
@@ -56,15 +57,16 @@ constexpr int kNMax = kTmemCols / 2;  // N of one MMA
 template <int P>
 struct Stage {
   static constexpr int A = 128 * 32 * 2 * P;    // 128 rows of one 16-wide K chunk, all planes
-  static constexpr int B = kNMax * 32 * 2 * P;  // up to kNMax rows
-  static constexpr int ctas_per_sm = P == 2 ? kCtas : (kCtas < 3 ? kCtas : 3);
+  static constexpr int B = kNMax * 32 * 3 * P;  // up to kNMax complex rows, [re; im; -re] per part
+  static constexpr int want = P == 2 ? kCtas : (kCtas < 3 ? kCtas : 3);
+  static constexpr int fit = ((220 * 1024 / want) / 1024) * 1024;
   // ring: what the SM's shared memory allows per CTA, at least two chunks
-  static constexpr int ring = ((220 * 1024 / ctas_per_sm) / 1024) * 1024 > 2 * (A + B)
-                                  ? ((220 * 1024 / ctas_per_sm) / 1024) * 1024
-                                  : 2 * (A + B);
-  static constexpr int bytes = A + B;
+  static constexpr int ring = fit > 2 * (A + B) ? fit : 2 * (A + B);
+  // CTAs that actually fit an SM with that ring (static shared memory and the
+  // per-CTA reservation included), at most the requested count
+  static constexpr int fits = (228 * 1024) / (ring + 2048);
+  static constexpr int ctas_per_sm = want < fits ? want : fits;
 };
-constexpr unsigned long long kTimeoutNs = 4000000000ull;
 
 __host__ __device__ inline int pad16(int x) { return (x + 15) & ~15; }
 __host__ __device__ inline int mrows_of(int rows) { return rows <= 64 ? 64 : 128; }
@@ -72,16 +74,21 @@ __host__ __device__ inline int ntiles_of(int rows) { return rows <= 64 ? 1 : (ro
 // rows stored for M tile t of a static operand with `rows` rows (no padding)
 __host__ __device__ inline int tile_rows(int rows, int t) { return rows - 128 * t < 128 ? rows - 128 * t : 128; }
 
-// element offset of (row, k) in a dynamic B operand: [kchunk][kNMax-row tile]
-// [plane][rows_t x 16], rows_t = min(kNMax, rows - kNMax t), so that the rows
-// of one N slice of one chunk form one contiguous block
-template <int PL>
-__host__ __device__ inline int64_t dyn_off(int row, int k, int plane, int rows) {
+// element offset of (complex row, k) in a dynamic B operand (E^T or T).
+// Layout: [kchunk][kNMax-row tile t][part][3 rows_t x 16], rows_t =
+// min(kNMax, rows - kNMax t), where the 3 rows_t rows of a part block are the
+// part's re rows, then its im rows, then its re rows negated (which = 0, 1,
+// 2), each block in the K-major core-matrix layout.  One N slice of one chunk
+// is then one contiguous block, and the MMA pair of a complex product reads
+// rows [0, 2 rows_t) = [re; im] and rows [rows_t, 3 rows_t) = [im; -re].
+template <int P>
+__host__ __device__ inline int64_t dyn_off(int row, int k, int part, int which, int rows) {
   const int kc = k >> 4, k16 = k & 15;
   const int t = (int)((unsigned)row / kNMax), r = (int)((unsigned)row % kNMax);  // row >= 0
   const int rows_t = min(kNMax, rows - kNMax * t);
-  return (int64_t)kc * PL * rows * 16 + (int64_t)t * PL * kNMax * 16 + (int64_t)plane * rows_t * 16 +
-         (r >> 3) * 128 + (k16 >> 3) * 64 + (r & 7) * 8 + (k16 & 7);
+  const int R = which * rows_t + r;
+  return (int64_t)kc * P * 3 * rows * 16 + (int64_t)t * P * 3 * kNMax * 16 + (int64_t)part * 3 * rows_t * 16 +
+         (R >> 3) * 128 + (k16 >> 3) * 64 + (R & 7) * 8 + (k16 & 7);
 }
 
 // element offset of (row, k) in a [kchunk][plane][rows x 16] block
@@ -168,59 +175,7 @@ __global__ void tc_pack_kernel(PackArgs p) {
 }
 
 // ---------------------------------------------------------------- PTX helpers
-__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline uint64_t make_desc(uint32_t saddr) {
-  // K-major, no swizzle: LBO (next core matrix along K) = 128 B,
-  // SBO (next 8-row group) = 256 B, descriptor version 1
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-__device__ inline uint32_t make_idesc(int M, int N, int neg_a) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg_a << 13) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ inline void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-__device__ inline void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_u32(bar)));
-}
-
-__device__ inline unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// bounded wait on an mbarrier phase; false on timeout
-__device__ inline bool wait_bar(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = kTimeoutNs) {
-  const uint32_t a = smem_u32(bar);
-  uint32_t done = 0;
-  unsigned long long t0 = 0;
-  for (uint32_t it = 0;; ++it) {
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity));
-    if (done) return true;
-    if ((it & 255) == 0) {
-      unsigned long long t = now_ns();
-      if (it == 0)
-        t0 = t;
-      else if (t - t0 > limit_ns)
-        return false;
-    }
-  }
-}
+using namespace tcx;  // smem_u32, make_desc, make_idesc, mma, commit, now_ns, wait_bar (tc_ptx.cuh)
 
 // L2 policies: streamed static operands go first, the per-CTA E/T scratch last
 __device__ inline uint64_t policy_evict_first() {
@@ -290,15 +245,24 @@ __device__ inline void split16(const float* x, uint32_t (*o)[8]) {
 template <int P>
 __device__ inline void store_row16(__nv_bfloat16* blk, int row, int k, int rows, const float* re,
                                    const float* im, uint64_t policy) {
-  constexpr int PL = 2 * P;
-  uint32_t h[PL][8];
-  split16<P>(re, h);
-  split16<P>(im, h + P);
+  uint32_t hr[P][8], hi[P][8];
+  split16<P>(re, hr);
+  split16<P>(im, hi);
 #pragma unroll
-  for (int pl = 0; pl < PL; ++pl) {
-    st_v4_last(blk + dyn_off<PL>(row, k, pl, rows), make_uint4(h[pl][0], h[pl][1], h[pl][2], h[pl][3]), policy);
-    st_v4_last(blk + dyn_off<PL>(row, k + 8, pl, rows), make_uint4(h[pl][4], h[pl][5], h[pl][6], h[pl][7]),
-               policy);
+  for (int part = 0; part < P; ++part) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t* r4 = hr[part] + 4 * half;
+      const uint32_t* i4 = hi[part] + 4 * half;
+      // splitting is odd-symmetric, so the parts of -re are the negated parts of re
+      const uint32_t sgn = 0x80008000u;
+      st_v4_last(blk + dyn_off<P>(row, k + 8 * half, part, 0, rows), make_uint4(r4[0], r4[1], r4[2], r4[3]),
+                 policy);
+      st_v4_last(blk + dyn_off<P>(row, k + 8 * half, part, 1, rows), make_uint4(i4[0], i4[1], i4[2], i4[3]),
+                 policy);
+      st_v4_last(blk + dyn_off<P>(row, k + 8 * half, part, 2, rows),
+                 make_uint4(r4[0] ^ sgn, r4[1] ^ sgn, r4[2] ^ sgn, r4[3] ^ sgn), policy);
+    }
   }
 }
 
@@ -325,6 +289,17 @@ struct TcArgs {
   unsigned long long* queue;
   int* err;
   int stall;                 // test hook: CTA 0 lets one bounded wait run out mid-GEMM
+  unsigned long long* prof;  // optional [kProfN] cycle counters summed over CTAs
+};
+
+// Phase counters of the profiling switch (qk_debug_tc_profile): clock64
+// cycles of thread 0 in its copy waits, ring waits and issue loop, and of
+// the CTA (as seen by thread 0) waiting for the MMAs, in the epilogue and at
+// the barrier after it; plus GEMM, chunk and tile counts.
+enum TcProfIdx { TP_ISSUE = 0, TP_WFULL, TP_WRING, TP_DONE, TP_EPI, TP_SYNC, TP_GEMMS, TP_CHUNKS, TP_TILES, kProfN };
+struct TcProf {  // in shared memory, written by thread 0 only
+  unsigned long long v[kProfN];
+  unsigned long long t;  // last mark
 };
 
 constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
@@ -332,6 +307,14 @@ constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
 // test hook (qk_debug_stall_next_split): the next tensor-core launch lets one
 // bounded wait run out
 std::atomic<int> g_stall_next{0};
+// profiling switch (qk_debug_tc_profile) and the counters of the last
+// profiled launch on this thread
+std::atomic<int> g_tc_profile{0};
+// test knob (qk_debug_tc_max_ctas): cap on the grid of the tensor-core kernel (0: none)
+std::atomic<int> g_tc_max_ctas{0};
+thread_local unsigned long long g_tc_prof_last[kProfN] = {};
+thread_local int g_tc_prof_ctas = 0;
+thread_local unsigned long long* g_tc_prof_pending = nullptr;
 
 struct __align__(8) TcShared {
   uint64_t full[kSlots];
@@ -352,13 +335,18 @@ struct __align__(8) TcShared {
 struct Ring {
   uint32_t produced = 0, released = 0;
   uint32_t issued = 0, waited = 0;  // chunks whose copies were issued / whose copies have landed
-  uint32_t head = 0, tail = 0;  // bytes ever produced / reclaimed
+  // bytes ever produced / reclaimed: 64-bit, because a CTA streams far more
+  // than 4 GiB through its ring in a large Gram, and the position
+  // head % ring_bytes is only continuous while head does not wrap
+  unsigned long long head = 0, tail = 0;
   uint32_t off[kSlots], len[kSlots];
 };
 
-__device__ inline bool ring_release(TcShared& sh, Ring& r) {
+__device__ inline bool ring_release(TcShared& sh, Ring& r, TcProf* pf) {
   const uint32_t j = r.released, slot = j % kSlots;
+  const unsigned long long t0 = pf ? clock64() : 0ull;
   if (!wait_bar(&sh.empty[slot], (j / kSlots) & 1)) return false;
+  if (pf) pf->v[TP_WRING] += clock64() - t0;
   r.tail += r.len[slot];
   ++r.released;
   return true;
@@ -371,9 +359,16 @@ __device__ inline bool ring_release(TcShared& sh, Ring& r) {
 template <int P>
 __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg, const char* gA,
                          uint32_t a_bytes, int a_rows, const char* gB, uint32_t b_bytes, int64_t b_stride,
-                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b, bool& stall) {
-  const uint32_t id_pos = make_idesc(M, N, 0), id_neg = make_idesc(M, N, 1);
-  const uint32_t t_re = sh.tmem, t_im = sh.tmem + N;
+                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b, bool& stall,
+                         TcProf* pf) {
+  const unsigned long long t_in = pf ? clock64() : 0ull;
+  if (pf) {
+    pf->v[TP_GEMMS] += 1;
+    pf->v[TP_CHUNKS] += nchunks;
+  }
+  // one accumulator [re | im] of 2N columns: every MMA has N' = 2N
+  const uint32_t id_pos = make_idesc(M, 2 * N, 0), id_neg = make_idesc(M, 2 * N, 1);
+  const uint32_t t_acc = sh.tmem;
   // The MMA reads M rows of every A plane; the planes hold a_rows <= M rows,
   // so the last plane's read runs (M - a_rows) rows past the A block.  The
   // ring reserves that span (the extra rows feed unused accumulator rows).
@@ -384,11 +379,11 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
   auto top_up = [&](uint32_t limit) -> bool {
     while (p < nchunks) {
       const uint32_t gi = g0 + p;
-      const uint32_t pos = rg.head % ring_bytes;
+      const uint32_t pos = (uint32_t)(rg.head % (unsigned long long)Stage<P>::ring);
       const uint32_t pad = pos + size > ring_bytes ? ring_bytes - pos : 0;
       while ((rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) &&
              rg.released < limit)
-        if (!ring_release(sh, rg)) return false;
+        if (!ring_release(sh, rg, pf)) return false;
       if (rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) break;
       const uint32_t slot = gi % kSlots, off = (pos + pad) % ring_bytes;
       rg.off[slot] = off;
@@ -412,12 +407,17 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
       stall = false;
       if (!wait_bar(&sh.stall, 0, 10000000ull)) return false;
     }
-    if (!wait_bar(&sh.full[slot], (gi / kSlots) & 1)) return false;
+    {
+      const unsigned long long tw = pf ? clock64() : 0ull;
+      if (!wait_bar(&sh.full[slot], (gi / kSlots) & 1)) return false;
+      if (pf) pf->v[TP_WFULL] += clock64() - tw;
+    }
     rg.waited = gi + 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // bytes per plane: A is stored with a_rows rows (rows of the M tile past
     // a_rows read other data and only feed accumulator rows that are unused)
-    const uint32_t pa = (uint32_t)a_rows * 32, pb = (uint32_t)N * 32;
+    // B part y is the block [re; im; -re] of 3N rows (32 bytes per row)
+    const uint32_t pa = (uint32_t)a_rows * 32, pbp = (uint32_t)N * 96;
     const uint32_t a0 = smem_u32(ring + rg.off[slot]), b0 = a0 + a_span;
     // cross terms (x part, y part) kept
     constexpr int NT = P == 2 ? 3 : 6;
@@ -427,12 +427,10 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const uint64_t ar = make_desc(a0 + xs[t] * pa), ai = make_desc(a0 + (P + xs[t]) * pa);
-      const uint64_t br = make_desc(b0 + ys[t] * pb), bi = make_desc(b0 + (P + ys[t]) * pb);
-      // re += Ar Br - Ai Bi ; im += Ar Bi + Ai Br
-      mma(t_re, ar, br, id_pos, t > 0 || acc);
-      mma(t_re, ai, bi, id_neg, 1);
-      mma(t_im, ar, bi, id_pos, t > 0 || acc);
-      mma(t_im, ai, br, id_pos, 1);
+      const uint32_t bp = b0 + ys[t] * pbp;
+      // [re | im] += Ar [Br; Bi]^T ;  [re | im] += -Ai [Bi; -Br]^T
+      mma(t_acc, ar, make_desc(bp), id_pos, t > 0 || acc);
+      mma(t_acc, ai, make_desc(bp + (uint32_t)N * 32), id_neg, 1);
     }
     commit(&sh.empty[slot]);
     // refill behind this chunk: chunks before it may be reclaimed
@@ -440,6 +438,7 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
   }
   commit(&sh.done);
   rg.produced = g0 + nchunks;
+  if (pf) pf->v[TP_ISSUE] += clock64() - t_in;
   return true;
 }
 
@@ -461,7 +460,8 @@ __device__ inline void sync_after_epilogue() {
 template <int P>
 __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_kernel(TcArgs a) {
   constexpr int kPlanes = 2 * P;
-  constexpr int kRowBytes = 32 * kPlanes;
+  constexpr int kRowBytes = 32 * kPlanes;   // static operand: bytes per row of a 16-wide K chunk
+  constexpr int kRowBytesB = 96 * P;        // dynamic operand: [re; im; -re] per part
   extern __shared__ __align__(1024) char dyn[];
   __shared__ TcShared sh;
   char* stage = dyn;
@@ -490,6 +490,18 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
   Ring rg;                  // operand ring (thread 0)
   bool stall = a.stall && blockIdx.x == 0;  // test hook, first GEMM of >= 2 chunks
+  __shared__ TcProf s_prof;
+  if (a.prof && tid == 0) {
+    for (int f = 0; f < kProfN; ++f) s_prof.v[f] = 0ull;
+    s_prof.t = clock64();
+  }
+  auto mark = [&](int what) {
+    if (a.prof && tid == 0) {
+      const unsigned long long t = clock64();
+      s_prof.v[what] += t - s_prof.t;
+      s_prof.t = t;
+    }
+  };
   const uint32_t ring_bytes = Stage<P>::ring;
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
@@ -500,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     __syncthreads();
     const int64_t tile = sh.tile;
     if (tile >= a.n_tiles || sh.abort) break;
+    if (a.prof && tid == 0) s_prof.v[TP_TILES] += 1;
     // ---- decode the tile: bra i, kets j[0..nk), output slots
     int i, nk = 0;
     int jj[kG];
@@ -522,12 +535,13 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     // ---- E_0 = [1]: Et blocks of 16 x 16 (one chunk), only (0, 0) = 1
     for (int q = 0; q < nk; ++q) {
       __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
-      for (int e = tid; e < kPlanes * 16 * 16; e += kThreads) et[e] = __float2bfloat16_rn(0.f);
+      for (int e = tid; e < 3 * P * 16 * 16; e += kThreads) et[e] = __float2bfloat16_rn(0.f);
     }
     __syncthreads();
     if (tid < nk) {
       __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + tid * a.et_stride);
-      et[dyn_off<kPlanes>(0, 0, 0, 16)] = __float2bfloat16_rn(1.f);
+      et[dyn_off<P>(0, 0, 0, 0, 16)] = __float2bfloat16_rn(1.f);    // re part 0
+      et[dyn_off<P>(0, 0, 0, 2, 16)] = __float2bfloat16_rn(-1.f);   // its negation
     }
     sync_after_epilogue();
     const int32_t* da = a.a_dims + (int64_t)i * (n + 1);
@@ -559,22 +573,24 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
               const int nh = min(kNMax, ap - h0);
               if (tid == 0) {
                 const char* gA = bt + (int64_t)t * (bp / 16) * 128 * kRowBytes;
-                const char* gB = et + (int64_t)h0 * kRowBytes;
+                const char* gB = et + (int64_t)h0 * kRowBytesB;
                 const int rt = tile_rows(rows, t);
-                if (!run_gemm<P>(sh, stage, ring_bytes, rg, gA, rt * kRowBytes, rt, gB, nh * kRowBytes,
-                                 (int64_t)ap * kRowBytes, bp / 16, mr, nh, pol_first, pol_last, stall)) {
+                if (!run_gemm<P>(sh, stage, ring_bytes, rg, gA, rt * kRowBytes, rt, gB, nh * kRowBytesB,
+                                 (int64_t)ap * kRowBytesB, bp / 16, mr, nh, pol_first, pol_last, stall, a.prof ? &s_prof : nullptr)) {
                   sh.abort = 1;
                   atomicExch(a.err, 1);
                 }
               }
               __syncthreads();
               if (sh.abort) goto finish;
+              if (a.prof && tid == 0) s_prof.t = clock64();
               if (!wait_bar(&sh.done, done_phase & 1)) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
               ++done_phase;
               asm volatile("tcgen05.fence::after_thread_sync;");
+              mark(TP_DONE);
               {
                 const int r = acc_row(mr);
                 const int R = t * 128 + r;
@@ -590,7 +606,9 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                   }
                 }
               }
+              mark(TP_EPI);
               sync_after_epilogue();
+              mark(TP_SYNC);
               if (sh.abort) goto finish;
             }
           }
@@ -602,21 +620,23 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
           for (int h0 = 0; h0 < ntot; h0 += kNMax) {
             const int nh = min(kNMax, ntot - h0);
             if (tid == 0) {
-              const char* gB = T_buf + (int64_t)h0 * kRowBytes;
-              if (!run_gemm<P>(sh, stage, ring_bytes, rg, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytes,
-                               (int64_t)ntot * kRowBytes, (2 * ap) / 16, mr, nh, pol_first, pol_last, stall)) {
+              const char* gB = T_buf + (int64_t)h0 * kRowBytesB;
+              if (!run_gemm<P>(sh, stage, ring_bytes, rg, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytesB,
+                               (int64_t)ntot * kRowBytesB, (2 * ap) / 16, mr, nh, pol_first, pol_last, stall, a.prof ? &s_prof : nullptr)) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
             }
             __syncthreads();
             if (sh.abort) goto finish;
+            if (a.prof && tid == 0) s_prof.t = clock64();
             if (!wait_bar(&sh.done, done_phase & 1)) {
               sh.abort = 1;
               atomicExch(a.err, 1);
             }
             ++done_phase;
             asm volatile("tcgen05.fence::after_thread_sync;");
+            mark(TP_DONE);
             const int r = acc_row(mr);
             const uint32_t lane_base = (uint32_t)((tid >> 5) * 32) << 16;
             for (int q = q0; q < q1; ++q) {
@@ -645,7 +665,9 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                 }
               }
             }
+            mark(TP_EPI);
             sync_after_epilogue();
+            mark(TP_SYNC);
             if (sh.abort) goto finish;
           }
         }
@@ -664,6 +686,8 @@ finish:
     commit(&sh.drain);
     wait_bar(&sh.drain, 0);
   }
+  if (a.prof && tid == 0)
+    for (int f = 0; f < kProfN; ++f) atomicAdd(a.prof + f, s_prof.v[f]);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -830,7 +854,6 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
                     int64_t P_pairs, double* dK, int64_t ldk, cudaStream_t st, int** err_out,
                     const TcSchedule& sch, int64_t i_lim, int64_t j_lim) {
   *err_out = nullptr;
-  constexpr int kPlanes = 2 * P;
   qk_status rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(A), st);
   if (rc != QK_OK) return rc;
   rc = ensure_tc_arena<P>(const_cast<qk_mps_batch*>(B), st);
@@ -856,10 +879,12 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   // scratch: `kets` Et blocks (<= 128 x 128) + T (<= 128 rows x 256 K), bf16 planes
   const int chi = std::max(A->chi_cap, B->chi_cap);
   const int cp = pad16(chi);
-  const int64_t et_stride = (int64_t)cp * cp * 2 * kPlanes + 256;
-  const int64_t t_bytes = (int64_t)128 * 2 * cp * 2 * kPlanes;
+  // dynamic operands hold [re; im; -re] per part: 3 P bf16 rows per complex row
+  const int64_t et_stride = (int64_t)cp * cp * 2 * 3 * P + 256;
+  const int64_t t_bytes = (int64_t)128 * 2 * cp * 2 * 3 * P;
   const int64_t stride = ((kets * et_stride + t_bytes) + 1023) & ~int64_t(1023);
-  const int64_t ctas = std::min<int64_t>((int64_t)Stage<P>::ctas_per_sm * sms, n_tiles);
+  int64_t ctas = std::min<int64_t>((int64_t)Stage<P>::ctas_per_sm * sms, n_tiles);
+  if (g_tc_max_ctas.load() > 0) ctas = std::min<int64_t>(ctas, g_tc_max_ctas.load());
   char* scratch = nullptr;
   int32_t* d_tiles = nullptr;
   unsigned long long* queue = nullptr;
@@ -896,6 +921,13 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.queue = queue;
   a.err = err;
   a.stall = g_stall_next.exchange(0);
+  a.prof = nullptr;
+  if (g_tc_profile.load() && !g_tc_prof_pending) {
+    QK_CUDA(cudaMallocAsync(&a.prof, sizeof(unsigned long long) * kProfN, st));
+    QK_CUDA(cudaMemsetAsync(a.prof, 0, sizeof(unsigned long long) * kProfN, st));
+    g_tc_prof_pending = a.prof;
+    g_tc_prof_ctas = (int)ctas;
+  }
   const int smem = Stage<P>::ring;
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   QK_CUDA(cudaFuncSetAttribute(tc_overlap_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -921,6 +953,12 @@ qk_status tc_finish(int* err, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(err, st);
+  if (g_tc_prof_pending) {
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g_tc_prof_last, g_tc_prof_pending, sizeof(g_tc_prof_last), cudaMemcpyDeviceToHost);
+    cudaFree(g_tc_prof_pending);
+    g_tc_prof_pending = nullptr;
+  }
   if (e != cudaSuccess) return cuda_fail(e, "tc_overlap_kernel");
   if (herr) return fail(QK_ERR_TIMEOUT, "tc_overlap_kernel: a bounded wait ran out");
   return QK_OK;
@@ -1188,5 +1226,22 @@ qk_status pairs_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, c
 
 extern "C" qk_status qk_debug_stall_next_split(int32_t on) {
   qk::g_stall_next.store(on ? 1 : 0);
+  return QK_OK;
+}
+
+extern "C" qk_status qk_debug_tc_profile(int32_t on) {
+  qk::g_tc_profile.store(on ? 1 : 0);
+  return QK_OK;
+}
+
+extern "C" qk_status qk_last_tc_profile(double* counters, int32_t* ctas) {
+  if (counters)
+    for (int f = 0; f < qk::kProfN; ++f) counters[f] = (double)qk::g_tc_prof_last[f];
+  if (ctas) *ctas = qk::g_tc_prof_ctas;
+  return QK_OK;
+}
+
+extern "C" qk_status qk_debug_tc_max_ctas(int32_t ctas) {
+  qk::g_tc_max_ctas.store(ctas > 0 ? ctas : 0);
   return QK_OK;
 }

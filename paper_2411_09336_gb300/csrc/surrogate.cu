@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "qk_internal.h"
+#include "tc_ptx.cuh"
 
 struct qk_surrogate {
   int device = 0;
@@ -272,10 +273,164 @@ __global__ void copy_block_kernel(const double* v, int64_t i0, int64_t cnt, int 
 
 inline int blocks(int64_t n, int t = 256) { return (int)std::min<int64_t>((n + t - 1) / t, 4096); }
 
+// ---- the same GEMM on the tensor cores (bf16 operands) ---------------------
+// One CTA computes a 128 x 128 tile of C with one tcgen05.mma (kind::f16,
+// M = N = 128, K = 16) per 16-wide K chunk, FP32 accumulation in TMEM.  The
+// 128 threads stage chunk c of A (row m0 + tid) and B (column n0 + tid),
+// rounded to bf16 as the SIMT kernel rounds them, into a 4-stage ring in the
+// K-major core-matrix layout (8 rows x 16 bytes, no swizzle); thread 0 issues
+// the MMA and commits it to the stage's mbarrier, which the threads wait for
+// (bounded) before they overwrite that stage.  Epilogue: tcgen05.ld -> bias
+// -> ReLU -> C.  A wait that runs out sets g_tc_gemm_err and the CTA drains
+// its MMAs before it frees the TMEM.
+constexpr int kGT = 128, kGStages = 4, kGThreads = 128;
+constexpr int kGStageBytes = 2 * kGT * 16 * 2;  // A and B blocks, bf16
+
+__device__ int g_tc_gemm_err;
+
+struct __align__(8) GemmShared {
+  uint64_t bar[kGStages];
+  uint64_t done;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ inline int core_off(int r, int k) { return (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
+
+__global__ void __launch_bounds__(kGThreads, 4) tc_gemm_kernel(int M, int N, int K, const float* A, int64_t sam,
+                                                                int64_t sak, const float* B, int64_t sbk,
+                                                                int64_t sbn, float* C, int64_t ldc,
+                                                                const float* bias, int relu) {
+  using namespace tcx;
+  extern __shared__ __align__(1024) char gdyn[];
+  __shared__ GemmShared sh;
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
+  if (tid < 32) tmem_alloc(&sh.tmem, kGT);
+  if (tid == 0) {
+    for (int s = 0; s < kGStages; ++s) mbar_init(&sh.bar[s], 1);
+    mbar_init(&sh.done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    sh.abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sh.tmem;
+  const uint32_t idesc = make_idesc(kGT, kGT, 0);
+  const int nk = (K + 15) / 16;
+  const int m = m0 + tid, n = n0 + tid;
+  float va[16], vb[16];
+  auto fetch = [&](int c) {
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const int k = c * 16 + kk;
+      va[kk] = (m < M && k < K) ? A[(int64_t)m * sam + (int64_t)k * sak] : 0.f;
+      vb[kk] = (n < N && k < K) ? B[(int64_t)k * sbk + (int64_t)n * sbn] : 0.f;
+    }
+  };
+  if (nk > 0) fetch(0);
+  for (int c = 0; c < nk; ++c) {
+    const int s = c % kGStages;
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(gdyn + s * kGStageBytes);
+    __nv_bfloat16* sb = sa + kGT * 16;
+    // the MMA that read this stage (chunk c - kGStages) must be done
+    if (c >= kGStages && !wait_bar(&sh.bar[s], ((c / kGStages) - 1) & 1)) sh.abort = 1;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      __align__(16) __nv_bfloat16 ha[8], hb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        ha[i] = __float2bfloat16_rn(va[8 * half + i]);
+        hb[i] = __float2bfloat16_rn(vb[8 * half + i]);
+      }
+      *reinterpret_cast<uint4*>(sa + core_off(tid, 8 * half)) = *reinterpret_cast<const uint4*>(ha);
+      *reinterpret_cast<uint4*>(sb + core_off(tid, 8 * half)) = *reinterpret_cast<const uint4*>(hb);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (sh.abort) break;
+    if (c + 1 < nk) fetch(c + 1);  // overlaps the MMA below
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      mma(tmem, make_desc(smem_u32(sa)), make_desc(smem_u32(sb)), idesc, c > 0 ? 1u : 0u);
+      commit(&sh.bar[s]);
+    }
+  }
+  if (tid == 0) commit(&sh.done);  // arrives once every MMA issued above is done
+  __syncthreads();
+  if (!wait_bar(&sh.done, 0)) sh.abort = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (!sh.abort && nk > 0) {
+    const int w = tid >> 5, lane = tid & 31;
+    const int row = m0 + 32 * w + lane;
+    const uint32_t lane_base = (uint32_t)(32 * w) << 16;
+    for (int c0 = 0; c0 < kGT; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + lane_base + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row < M)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = n0 + c0 + i;
+          if (col < N) {
+            float v = __uint_as_float(r[i]) + (bias ? bias[col] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            C[(int64_t)row * ldc + col] = v;
+          }
+        }
+    }
+  } else if (!sh.abort) {
+    // K = 0: C = act(bias)
+    const int row = m0 + tid;
+    if (row < M)
+      for (int col = n0; col < min(N, n0 + kGT); ++col) {
+        float v = bias ? bias[col] : 0.f;
+        if (relu) v = fmaxf(v, 0.f);
+        C[(int64_t)row * ldc + col] = v;
+      }
+  }
+  if (sh.abort && tid == 0) atomicExch(&g_tc_gemm_err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (tid < 32) tmem_dealloc(tmem, kGT);
+}
+
 void gemm(cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B,
           int64_t sbk, int64_t sbn, float* C, int64_t ldc, const float* bias, int relu, int bf16) {
+  if (bf16) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGStages * kGStageBytes);
+      attr = true;
+    }
+    dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
+    tc_gemm_kernel<<<grid, kGThreads, kGStages * kGStageBytes, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc,
+                                                                    bias, relu);
+    return;
+  }
   dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM);
   gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu, bf16);
+}
+
+// Reads and clears the tensor-core GEMM's error word (synchronises the stream).
+qk_status gemm_status(cudaStream_t st, const char* who) {
+  int h = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&h, g_tc_gemm_err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  if (h) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_tc_gemm_err, &zero, sizeof(int));
+    return fail(QK_ERR_TIMEOUT, std::string(who) + ": a bounded wait of the tensor-core GEMM ran out");
+  }
+  return QK_OK;
 }
 
 // Work buffers for a minibatch of P pairs.
@@ -543,6 +698,7 @@ extern "C" qk_status qk_surrogate_loss_grad(qk_surrogate* net, const double* Xa,
   w.release(st);
   in.release(st);
   cudaStreamSynchronize(st);
+  if (rc == QK_OK) rc = gemm_status(st, "qk_surrogate_loss_grad");
   return rc;
 }
 
@@ -622,6 +778,7 @@ extern "C" qk_status qk_surrogate_train(qk_surrogate* net, const double* Xa, int
   if (dt) cudaFreeAsync(dt, st);
   in.release(st);
   cudaStreamSynchronize(st);
+  if (rc == QK_OK) rc = gemm_status(st, "qk_surrogate_train");
   return rc;
 }
 
@@ -654,6 +811,7 @@ extern "C" qk_status qk_surrogate_predict(const qk_surrogate* net, const double*
   if (dy) cudaFreeAsync(dy, st);
   in.release(st);
   cudaStreamSynchronize(st);
+  if (rc == QK_OK) rc = gemm_status(st, "qk_surrogate_predict");
   return rc;
 }
 
@@ -788,5 +946,6 @@ extern "C" qk_status qk_gram_surrogate(const qk_surrogate* net, const qk_mps_bat
   in.release(st);
   cudaStreamSynchronize(st);
   if (rc == QK_OK && n_accepted) *n_accepted = n_acc;
+  if (rc == QK_OK) rc = gemm_status(st, "qk_gram_surrogate");
   return rc;
 }

@@ -201,3 +201,22 @@ def test_bounded_wait_runs_out_and_device_stays_usable(qk):
     assert ei.value.status == qk.QK_ERR_TIMEOUT
     K, _ = qk.qk_gram(A, prec="split")
     check(K.cpu().numpy(), Kref)
+
+
+def test_one_cta_streams_more_than_4gib_exact_and_deterministic(qk):
+    """One CTA contracting all 276 pairs of 24 n=165 states streams more than
+    4 GiB of operands through its shared-memory ring (about 20 MB per pair);
+    the ring's byte positions must stay consistent past 2^32 bytes.  The
+    split Gram must match the FP64 path and repeat bit for bit."""
+    w = workloads.c165()
+    A = qk.qk_build_states(w.X[:24], w.d, w.reps, w.gamma, w.chi_max, w.eps)
+    K64 = qk.qk_gram(A, prec="fp64")[0].cpu().numpy()
+    try:
+        qk.qk_debug_tc_max_ctas(1)
+        for prec in PRECS:
+            K1 = qk.qk_gram(A, prec=prec)[0].cpu().numpy()
+            K2 = qk.qk_gram(A, prec=prec)[0].cpu().numpy()
+            assert np.array_equal(K1, K2), prec
+            check(K1, K64, rel=2e-3)
+    finally:
+        qk.qk_debug_tc_max_ctas(0)

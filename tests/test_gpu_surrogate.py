@@ -134,3 +134,39 @@ def test_gram_surrogate_accepts_within_bound_and_falls_back(qk):
     assert np.array_equal(Ks[~acc], Kx[~acc])
     err = np.abs(np.log(Ks[acc]) - np.log(Kx[acc]))
     assert np.mean(err <= tol) >= 0.8
+
+
+def _bf16(x):
+    """Round to bf16 (nearest even) through FP32, as the kernels round GEMM
+    operands, and return float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    r = (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def test_bf16_forward_on_tensor_cores_matches_rounded_reference(qk):
+    """bf16 mode runs the layer GEMMs on the tensor cores (tcgen05, bf16
+    operands, FP32 accumulation).  Against an FP64 forward pass whose GEMM
+    operands are rounded to bf16 the same way, the predictions agree to FP32
+    accumulation rounding (several 128 x 128 output tiles, ragged K)."""
+    n, h, P = 37, 256, 700
+    rng = np.random.default_rng(21)
+    X = rng.normal(size=(90, n))
+    pairs = np.stack([rng.integers(0, 90, P), rng.integers(0, 90, P)], 1).astype(np.int32)
+    net = qk.qk_surrogate_create(2 * n, h, seed=9)
+    prm = net.get_params()
+    prm[2 * n * h:2 * n * h + h] = rng.normal(0, 0.2, h)
+    net.set_params(prm)
+    y = net.predict(X, X, pairs)
+    Pm = unpack(prm, 2 * n, h)
+    F = mlp.pair_features(X, X, pairs).astype(np.float32)
+    z1 = _bf16(F) @ _bf16(Pm["W1"]).T + Pm["b1"]
+    h1 = np.maximum(z1, 0.0).astype(np.float32)
+    z2 = _bf16(h1) @ _bf16(Pm["W2"]).T + Pm["b2"]
+    h2 = np.maximum(z2, 0.0).astype(np.float32)
+    yref = (_bf16(h2) @ _bf16(Pm["W3"]).T)[:, 0] + Pm["b3"][0]
+    scale = np.max(np.abs(yref))
+    err = np.abs(y - yref)
+    assert np.median(err) <= 1e-5 * scale
+    assert np.max(err) <= 2e-3 * scale
