@@ -47,10 +47,10 @@ BENCH_SCHEDULE = {"kets_per_tile": 1, "band": 128}
 # the n=165, d=6, chi_max=128 circuit with BENCH_SCHEDULE, from one ncu
 # capture of a smaller symmetric Gram of the same circuit (the capture's
 # dram__bytes_read.sum + dram__bytes_write.sum divided by its pairs; see
-# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 235.36 GB for the
+# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 256.10 GB for the
 # 11,476 pairs of a 152-state Gram).  Per-pair time is the same at 152 and
 # 1216 states, so the per-pair traffic is taken as independent of N.
-TC_DRAM_BYTES_PER_PAIR = 235.358644e9 / 11476
+TC_DRAM_BYTES_PER_PAIR = 256.102518784e9 / 11476
 
 
 def roofline_traffic(prec, schedule, pairs):
@@ -144,6 +144,30 @@ def gram_flops(dims: np.ndarray, diagonal: bool = False, order: str = "kernel") 
         cb = a1 * a0 * b0 + a1 * b0 * b1
         total += np.sum(np.minimum(ca, cb))
     return 16.0 * total
+
+
+def issued_macs(dims: np.ndarray, n_max: int = 64, products: int = 3) -> float:
+    """Real bf16 MACs the tensor-core kernel issues for the pairs i < j with
+    one ket per tile: per site, HS1 runs ceil(2 chi^b_k+1 / 128) M tiles (M =
+    64 when 2 chi^b_k+1 <= 64, else 128) against E^T, and HS2 one M tile
+    (M = 64 or 128 by chi^a_k+1) against T; bonds are padded to 16; every
+    K chunk issues 2 MMAs of width 2N per split product.  Per pair, site and
+    product: HS1 4 M ap bp n_tiles (K = bp), HS2 8 M' bp1 ap (K = 2 ap), with
+    ap = pad16(chi^a_k), bp = pad16(chi^b_k), bp1 = pad16(chi^b_k+1)."""
+    pad = lambda x: (x + 15) // 16 * 16
+    c = dims.astype(np.int64)
+    a0, a1 = pad(c[:, :-1]), pad(c[:, 1:])
+    rows = 2 * a1  # as a ket
+    M1 = np.where(rows <= 64, 64, 128)
+    nt = np.where(rows <= 64, 1, (rows + 127) // 128)
+    M2 = np.where(a1 <= 64, 64, 128)  # as a bra
+    ket1 = (nt * M1 * a0).astype(np.float64)        # HS1 ket factor (x ap of the bra)
+    bra1 = a0.astype(np.float64)
+    bra2 = (M2 * a0).astype(np.float64)             # HS2 bra factor (x bp1 of the ket)
+    ket2 = a1.astype(np.float64)
+    pre1 = np.cumsum(bra1, axis=0) - bra1
+    pre2 = np.cumsum(bra2, axis=0) - bra2
+    return float(products) * (4.0 * np.sum(ket1 * pre1) + 8.0 * np.sum(ket2 * pre2))
 
 
 FP64_DFMA_PER_CLK_PER_SM = 2  # GB300: 1.25 TFLOP/s FP64 at 152 SMs x 2.07 GHz
@@ -574,6 +598,8 @@ def run_ours(a):
                      "kernel": "tc_overlap_kernel", "peak_source": f"bf16_tflops_sustained ({src})",
                      "algorithmic_tflop_per_launch": flops / 1e12,
                      "kernel_order_tflop_per_launch": flops_kernel / 1e12,
+                     "issued_bf16_tflop_per_launch": 2.0 * issued_macs(dims) / 1e12,
+                     "issued_over_algorithmic": 2.0 * issued_macs(dims) / flops,
                      "kernel_ms_per_launch": kavg, "refine_ms_per_step": float(np.mean(refine_ms)),
                      "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a 152-state capture "
                                         "with the same schedule, per pair, times the launch's pairs") if traffic

@@ -268,10 +268,12 @@ qk_status qk_debug_stall_next_split(int32_t on);
 /* Profiling switch of the tensor-core overlap kernel (the paper has no
  * counterpart).  While `on`, every launch of the kernel sums per-CTA clock64
  * cycles by phase; qk_last_tc_profile returns those of the last launch on
- * this thread: counters[9] = thread 0's cycles inside the MMA-issue loop,
+ * this thread: counters[11] = thread 0's cycles inside the MMA-issue loop,
  * waiting for operand copies, waiting for ring space; the CTA's cycles
  * waiting for the MMAs, in the epilogue, at the barrier after it (all seen
- * by thread 0, summed over CTAs); then GEMMs, K-chunks and tiles processed.
+ * by thread 0, summed over CTAs); GEMMs, K-chunks and tiles processed; and
+ * thread 0's cycles in the ring bookkeeping and copy issue (ring waits
+ * included) and in issuing the MMAs of a chunk.
  * ctas: CTAs of that launch.  No synchronisation. */
 qk_status qk_debug_tc_profile(int32_t on);
 /* Test knob: caps the grid of the tensor-core overlap kernel at `ctas` CTAs

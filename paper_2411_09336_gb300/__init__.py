@@ -303,7 +303,8 @@ def qk_debug_stall_next_split(on: bool = True) -> None:
     _check(_lib.qk_debug_stall_next_split(1 if on else 0), "qk_debug_stall_next_split")
 
 
-TC_PHASES = ("issue", "wait_copies", "wait_ring", "wait_mma", "epilogue", "barrier", "gemms", "chunks", "tiles")
+TC_PHASES = ("issue", "wait_copies", "wait_ring", "wait_mma", "epilogue", "barrier", "gemms", "chunks", "tiles",
+             "topup", "mma")
 
 
 def qk_debug_tc_profile(on: bool = True) -> None:

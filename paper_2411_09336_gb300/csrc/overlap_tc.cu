@@ -9,19 +9,25 @@
 //   HS1: D1[(s,b'), a]   = Bt_j[(s,b'), b] . Et[b, a]        (A static, B = E)
 //   HS2: D2[a', (j,b')]  = Ah_i[a', (s,a)] . T[(s,a), (j,b')] (A static, B = T)
 // Every operand is stored K-major in 16-wide K chunks of 8x(16 B) core
-// matrices (no swizzle), as bf16 planes of re and im, each value split into
+// matrices (no swizzle), as bf16 parts of re and im, each value split into
 // P parts x = x0 + x1 (+ x2), x_{k+1} = bf16(x - x0 - .. - x_k):
 //   P = 2: residual <= 2^-17 |x|; products 00, 01, 10 (order >= 2^-8 kept,
-//          lo*lo dropped), 12 MMAs per 16-wide K chunk for a complex product;
+//          lo*lo dropped);
 //   P = 3: exact for any FP32 value; products 00, 01, 10, 02, 11, 20 (order
-//          >= 2^-16 kept), 24 MMAs per chunk.
-// re += Ar Br - Ai Bi (the minus via the A-negate bit), im += Ar Bi + Ai Br,
-// all accumulated in FP32 in TMEM.  The static (per-state) operands Bt/Ah are packed once
-// per batch (tc_pack_kernel); E and T live in a per-CTA global scratch that
-// the epilogue writes (tcgen05.ld -> split -> st.global) and the next GEMM
-// streams back with 1-D bulk copies.  One elected thread keeps a byte ring
-// of up to eight chunks of bulk copies in flight ahead of its MMAs; every wait is bounded in
-// time and reports QK_ERR_TIMEOUT instead of hanging.
+//          >= 2^-16 kept).
+// The static (per-state) operands Bt/Ah are packed once per batch
+// (tc_pack_kernel) as 2P planes (re parts, im parts).  The dynamic operands
+// E^T and T hold, per part, the rows [re; im; -re], so one MMA of width 2N
+// over rows [re; im] and one with the A-negate bit over rows [im; -re] add
+// [Ar Br - Ai Bi | Ar Bi + Ai Br] into a single FP32 accumulator [re | im]
+// in TMEM: 2 MMAs per product and K chunk.  E and T live in a per-CTA global
+// scratch that the epilogue writes (tcgen05.ld -> split -> st.global) and
+// the next GEMM streams back with 1-D bulk copies.  Within a CTA one producer
+// thread (warp 1) issues the bulk copies into a byte ring of up to eight
+// chunks and reclaims the space of chunks whose MMAs have completed, while
+// thread 0 waits for each chunk and issues its MMAs, so copy issue and MMA
+// issue overlap; three CTAs per SM overlap one another's epilogues.  Every
+// wait is bounded in time and reports QK_ERR_TIMEOUT instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -52,8 +58,15 @@ constexpr int kG = 4;            // kets per tile at most
 #define QK_TC_CTAS 4
 #endif
 constexpr int kCtas = QK_TC_CTAS;
-constexpr int kTmemCols = kCtas <= 2 ? 256 : 128;
-constexpr int kNMax = kTmemCols / 2;  // N of one MMA
+// complex columns of one MMA (its N' is 2 kNMax: [re | im]); the accumulator
+// takes 2 kNMax TMEM columns
+#ifndef QK_TC_NMAX
+#define QK_TC_NMAX (QK_TC_CTAS <= 2 ? 128 : 64)
+#endif
+constexpr int kNMax = QK_TC_NMAX;
+constexpr int kTmemCols = 2 * kNMax;
+static_assert(kNMax == 64 || kNMax == 128, "one MMA covers 64 or 128 complex columns");
+static_assert(kCtas * kTmemCols <= 512, "the CTAs of an SM share its 512 TMEM columns");
 template <int P>
 struct Stage {
   static constexpr int A = 128 * 32 * 2 * P;    // 128 rows of one 16-wide K chunk, all planes
@@ -296,13 +309,15 @@ struct TcArgs {
 // cycles of thread 0 in its copy waits, ring waits and issue loop, and of
 // the CTA (as seen by thread 0) waiting for the MMAs, in the epilogue and at
 // the barrier after it; plus GEMM, chunk and tile counts.
-enum TcProfIdx { TP_ISSUE = 0, TP_WFULL, TP_WRING, TP_DONE, TP_EPI, TP_SYNC, TP_GEMMS, TP_CHUNKS, TP_TILES, kProfN };
+enum TcProfIdx { TP_ISSUE = 0, TP_WFULL, TP_WRING, TP_DONE, TP_EPI, TP_SYNC, TP_GEMMS, TP_CHUNKS, TP_TILES, TP_TOPUP,
+                 TP_MMA, kProfN };
 struct TcProf {  // in shared memory, written by thread 0 only
   unsigned long long v[kProfN];
   unsigned long long t;  // last mark
 };
 
 constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
+constexpr int kProducer = 32;  // the thread (lane 0 of warp 1) that issues the bulk copies
 
 // test hook (qk_debug_stall_next_split): the next tensor-core launch lets one
 // bounded wait run out
@@ -325,6 +340,8 @@ struct __align__(8) TcShared {
   uint32_t tmem;
   int abort;
   int64_t tile;
+  uint32_t roff[kSlots];  // ring offset of the chunk in each slot (producer -> MMA thread)
+  uint32_t issued;        // chunks whose copies were issued (for the abort drain)
 };
 
 // Byte ring of operand chunks in shared memory (thread 0's bookkeeping).
@@ -332,75 +349,123 @@ struct __align__(8) TcShared {
 // g % kSlots; its A and B blocks sit contiguously at off[slot], len[slot]
 // bytes including any padding skipped at the ring's end.  Chunks are
 // reclaimed in order once the MMAs that read them have completed.
-struct Ring {
-  uint32_t produced = 0, released = 0;
-  uint32_t issued = 0, waited = 0;  // chunks whose copies were issued / whose copies have landed
-  // bytes ever produced / reclaimed: 64-bit, because a CTA streams far more
-  // than 4 GiB through its ring in a large Gram, and the position
-  // head % ring_bytes is only continuous while head does not wrap
-  unsigned long long head = 0, tail = 0;
-  uint32_t off[kSlots], len[kSlots];
+struct Ring {  // producer state
+  uint32_t produced = 0, released = 0;  // chunks issued / reclaimed so far
+  // The live chunks occupy the `used` bytes (padding included) that end at
+  // the write position `wpos`, circularly.  Both stay below the ring size, so
+  // nothing wraps however many bytes a CTA streams (a byte counter taken
+  // modulo the ring size, as an earlier version did, jumps when the counter
+  // wraps at 2^32 and places new chunks on live ones).
+  uint32_t wpos = 0, used = 0;
+  uint32_t len[kSlots];
 };
 
-__device__ inline bool ring_release(TcShared& sh, Ring& r, TcProf* pf) {
-  const uint32_t j = r.released, slot = j % kSlots;
-  const unsigned long long t0 = pf ? clock64() : 0ull;
-  if (!wait_bar(&sh.empty[slot], (j / kSlots) & 1)) return false;
-  if (pf) pf->v[TP_WRING] += clock64() - t0;
-  r.tail += r.len[slot];
-  ++r.released;
+// Operands of one GEMM: `nchunks` 16-wide K chunks of a static A block
+// (a_rows rows of 2P planes, a_bytes per chunk, consecutive) and a dynamic B
+// block (N complex rows as [re; im; -re] per part, b_bytes per chunk, chunk
+// stride b_stride); M accumulator rows.
+struct Gemm {
+  const char* gA;
+  uint32_t a_bytes;
+  int a_rows;
+  const char* gB;
+  uint32_t b_bytes;
+  int64_t b_stride;
+  int nchunks, M, N;
+};
+
+// The MMA reads M rows of every A plane; the planes hold a_rows <= M rows, so
+// the last plane's read runs (M - a_rows) rows past the A block.  The ring
+// reserves that span (the extra rows feed unused accumulator rows).
+template <int P>
+__device__ inline uint32_t a_span_of(const Gemm& g) {
+  return (uint32_t)(2 * P - 1) * g.a_rows * 32 + (uint32_t)g.M * 32;
+}
+
+// Bounded wait that also gives up once another thread of the CTA has aborted.
+__device__ inline bool wait_or_abort(TcShared& sh, uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 0) {
+      if (*(volatile int*)&sh.abort) return false;
+      const unsigned long long t = now_ns();
+      if (it == 0)
+        t0 = t;
+      else if (t - t0 > kTimeoutNs)
+        return false;
+    }
+  }
+}
+
+// Producer (one thread of warp 1): streams the chunks of one GEMM through the
+// ring with bulk copies, as far ahead as the ring's bytes and mbarrier slots
+// allow, and reclaims the space of chunks whose MMAs have completed.  Every
+// issued chunk is consumed in order by the MMA thread, so waiting for the
+// oldest live chunk always ends.
+template <int P>
+__device__ bool gemm_produce(TcShared& sh, char* ring, Ring& rg, const Gemm& g, uint64_t pol_a, uint64_t pol_b,
+                             TcProf* pf) {
+  const unsigned long long t_in = pf ? clock64() : 0ull;
+  constexpr uint32_t R = Stage<P>::ring;
+  const uint32_t a_span = a_span_of<P>(g), size = a_span + g.b_bytes;
+  const uint32_t g0 = rg.produced;
+  for (int p = 0; p < g.nchunks; ++p) {
+    const uint32_t gi = g0 + p;
+    const uint32_t pad = rg.wpos + size > R ? R - rg.wpos : 0;  // a chunk never straddles the end
+    const uint32_t need = pad + size;
+    while (rg.used + need > R || gi - rg.released >= (uint32_t)kSlots) {
+      const uint32_t j = rg.released, js = j % kSlots;
+      const unsigned long long t0 = pf ? clock64() : 0ull;
+      if (!wait_or_abort(sh, &sh.empty[js], (j / kSlots) & 1)) return false;
+      if (pf) pf->v[TP_WRING] += clock64() - t0;
+      rg.used -= rg.len[js];
+      ++rg.released;
+    }
+    const uint32_t slot = gi % kSlots, off = pad ? 0u : rg.wpos;
+    sh.roff[slot] = off;
+    rg.len[slot] = need;
+    rg.used += need;
+    rg.wpos = off + size == R ? 0u : off + size;
+    expect_tx(&sh.full[slot], g.a_bytes + g.b_bytes);
+    bulk_load(ring + off, g.gA + (int64_t)p * g.a_bytes, g.a_bytes, &sh.full[slot], pol_a);
+    bulk_load(ring + off + a_span, g.gB + (int64_t)p * g.b_stride, g.b_bytes, &sh.full[slot], pol_b);
+    sh.issued = gi + 1;
+  }
+  rg.produced = g0 + g.nchunks;
+  if (pf) pf->v[TP_TOPUP] += clock64() - t_in;
   return true;
 }
 
-// Streams `nchunks` K-chunks of (A block, B block) through the ring, keeping
-// as many bulk copies in flight as the ring holds, and issues the
-// 4 x (split products) MMAs per chunk into TMEM columns [0, N) (re) and
-// [N, 2N) (im).  Called by thread 0 only.
+// Consumer (thread 0): waits for each chunk and issues its split products,
+// 2 MMAs of width 2N per product into the accumulator [re | im] (TMEM columns
+// [0, 2N)), commits each chunk to its `empty` barrier and the GEMM to `done`.
 template <int P>
-__device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg, const char* gA,
-                         uint32_t a_bytes, int a_rows, const char* gB, uint32_t b_bytes, int64_t b_stride,
-                         int nchunks, int M, int N, uint64_t pol_a, uint64_t pol_b, bool& stall,
-                         TcProf* pf) {
+__device__ bool gemm_consume(TcShared& sh, char* ring, uint32_t& consumed, uint32_t& waited, const Gemm& g,
+                             bool& stall, TcProf* pf) {
   const unsigned long long t_in = pf ? clock64() : 0ull;
   if (pf) {
     pf->v[TP_GEMMS] += 1;
-    pf->v[TP_CHUNKS] += nchunks;
+    pf->v[TP_CHUNKS] += g.nchunks;
   }
-  // one accumulator [re | im] of 2N columns: every MMA has N' = 2N
-  const uint32_t id_pos = make_idesc(M, 2 * N, 0), id_neg = make_idesc(M, 2 * N, 1);
+  const uint32_t id_pos = make_idesc(g.M, 2 * g.N, 0), id_neg = make_idesc(g.M, 2 * g.N, 1);
   const uint32_t t_acc = sh.tmem;
-  // The MMA reads M rows of every A plane; the planes hold a_rows <= M rows,
-  // so the last plane's read runs (M - a_rows) rows past the A block.  The
-  // ring reserves that span (the extra rows feed unused accumulator rows).
-  const uint32_t a_span = (uint32_t)(2 * P - 1) * a_rows * 32 + (uint32_t)M * 32;
-  const uint32_t g0 = rg.produced, size = a_span + b_bytes;
-  int p = 0;  // chunks of this GEMM issued
-  // issue loads while space and slots allow, reclaiming only chunks < limit
-  auto top_up = [&](uint32_t limit) -> bool {
-    while (p < nchunks) {
-      const uint32_t gi = g0 + p;
-      const uint32_t pos = (uint32_t)(rg.head % (unsigned long long)Stage<P>::ring);
-      const uint32_t pad = pos + size > ring_bytes ? ring_bytes - pos : 0;
-      while ((rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) &&
-             rg.released < limit)
-        if (!ring_release(sh, rg, pf)) return false;
-      if (rg.head + pad + size - rg.tail > ring_bytes || gi - rg.released >= (uint32_t)kSlots) break;
-      const uint32_t slot = gi % kSlots, off = (pos + pad) % ring_bytes;
-      rg.off[slot] = off;
-      rg.len[slot] = pad + size;
-      rg.head += pad + size;
-      expect_tx(&sh.full[slot], a_bytes + b_bytes);
-      bulk_load(ring + off, gA + (int64_t)p * a_bytes, a_bytes, &sh.full[slot], pol_a);
-      bulk_load(ring + off + a_span, gB + (int64_t)p * b_stride, b_bytes, &sh.full[slot], pol_b);
-      rg.issued = gi + 1;
-      ++p;
-    }
-    return true;
-  };
-  if (!top_up(g0)) return false;
-  for (int c = 0; c < nchunks; ++c) {
+  const uint32_t a_span = a_span_of<P>(g);
+  // bytes per plane: A is stored with a_rows rows (rows of the M tile past
+  // a_rows read other data and only feed accumulator rows that are unused);
+  // B part y is the block [re; im; -re] of 3N rows (32 bytes per row)
+  const uint32_t pa = (uint32_t)g.a_rows * 32, pbp = (uint32_t)g.N * 96;
+  const uint32_t g0 = consumed;
+  for (int c = 0; c < g.nchunks; ++c) {
     const uint32_t gi = g0 + c, slot = gi % kSlots;
-    if (p <= c && !top_up(gi)) return false;  // reclaims everything before chunk c
     if (stall && c == 1) {
       // test hook: a wait on a barrier nothing arrives at runs out while
       // chunk 0's MMAs and the later chunks' copies are in flight
@@ -409,16 +474,14 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
     }
     {
       const unsigned long long tw = pf ? clock64() : 0ull;
-      if (!wait_bar(&sh.full[slot], (gi / kSlots) & 1)) return false;
+      if (!wait_or_abort(sh, &sh.full[slot], (gi / kSlots) & 1)) return false;
       if (pf) pf->v[TP_WFULL] += clock64() - tw;
     }
-    rg.waited = gi + 1;
+    waited = gi + 1;
+    const unsigned long long t_mma = pf ? clock64() : 0ull;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // bytes per plane: A is stored with a_rows rows (rows of the M tile past
-    // a_rows read other data and only feed accumulator rows that are unused)
-    // B part y is the block [re; im; -re] of 3N rows (32 bytes per row)
-    const uint32_t pa = (uint32_t)a_rows * 32, pbp = (uint32_t)N * 96;
-    const uint32_t a0 = smem_u32(ring + rg.off[slot]), b0 = a0 + a_span;
+    const uint32_t off = *(volatile uint32_t*)&sh.roff[slot];
+    const uint32_t a0 = smem_u32(ring + off), b0 = a0 + a_span;
     // cross terms (x part, y part) kept
     constexpr int NT = P == 2 ? 3 : 6;
     const int xs[6] = {0, 0, 1, 0, 1, 2};
@@ -430,14 +493,13 @@ __device__ bool run_gemm(TcShared& sh, char* ring, uint32_t ring_bytes, Ring& rg
       const uint32_t bp = b0 + ys[t] * pbp;
       // [re | im] += Ar [Br; Bi]^T ;  [re | im] += -Ai [Bi; -Br]^T
       mma(t_acc, ar, make_desc(bp), id_pos, t > 0 || acc);
-      mma(t_acc, ai, make_desc(bp + (uint32_t)N * 32), id_neg, 1);
+      mma(t_acc, ai, make_desc(bp + (uint32_t)g.N * 32), id_neg, 1);
     }
     commit(&sh.empty[slot]);
-    // refill behind this chunk: chunks before it may be reclaimed
-    if (!top_up(gi)) return false;
+    if (pf) pf->v[TP_MMA] += clock64() - t_mma;
   }
   commit(&sh.done);
-  rg.produced = g0 + nchunks;
+  consumed = g0 + g.nchunks;
   if (pf) pf->v[TP_ISSUE] += clock64() - t_in;
   return true;
 }
@@ -482,15 +544,18 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.stall)));
     asm volatile("fence.mbarrier_init.release.cluster;");
     sh.abort = 0;
+    sh.issued = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sh.tmem;
   const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
-  Ring rg;                  // operand ring (thread 0)
+  Ring rg;                       // operand ring (the producer thread's state)
+  uint32_t consumed = 0, waited = 0;  // the MMA thread's chunk counts
   bool stall = a.stall && blockIdx.x == 0;  // test hook, first GEMM of >= 2 chunks
   __shared__ TcProf s_prof;
+  TcProf* pf = a.prof ? &s_prof : nullptr;  // written by thread 0 and the producer (disjoint counters)
   if (a.prof && tid == 0) {
     for (int f = 0; f < kProfN; ++f) s_prof.v[f] = 0ull;
     s_prof.t = clock64();
@@ -502,7 +567,6 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
       s_prof.t = t;
     }
   };
-  const uint32_t ring_bytes = Stage<P>::ring;
   uint32_t done_phase = 0;  // completed GEMMs (all threads)
   char* scr = a.scratch + (int64_t)blockIdx.x * a.scratch_stride;
   char* T_buf = scr + (int64_t)a.kets * a.et_stride;
@@ -571,12 +635,14 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
           for (int t = 0; t < nt; ++t) {
             for (int h0 = 0; h0 < ap; h0 += kNMax) {
               const int nh = min(kNMax, ap - h0);
-              if (tid == 0) {
-                const char* gA = bt + (int64_t)t * (bp / 16) * 128 * kRowBytes;
-                const char* gB = et + (int64_t)h0 * kRowBytesB;
+              if (tid == 0 || tid == kProducer) {
                 const int rt = tile_rows(rows, t);
-                if (!run_gemm<P>(sh, stage, ring_bytes, rg, gA, rt * kRowBytes, rt, gB, nh * kRowBytesB,
-                                 (int64_t)ap * kRowBytesB, bp / 16, mr, nh, pol_first, pol_last, stall, a.prof ? &s_prof : nullptr)) {
+                const Gemm g{bt + (int64_t)t * (bp / 16) * 128 * kRowBytes, (uint32_t)(rt * kRowBytes), rt,
+                             et + (int64_t)h0 * kRowBytesB, (uint32_t)(nh * kRowBytesB),
+                             (int64_t)ap * kRowBytesB, bp / 16, mr, nh};
+                const bool ok = tid == 0 ? gemm_consume<P>(sh, stage, consumed, waited, g, stall, pf)
+                                         : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf);
+                if (!ok) {
                   sh.abort = 1;
                   atomicExch(a.err, 1);
                 }
@@ -619,10 +685,12 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
           const char* ah = a.a_arena + a.a_ah[(int64_t)i * n + k];
           for (int h0 = 0; h0 < ntot; h0 += kNMax) {
             const int nh = min(kNMax, ntot - h0);
-            if (tid == 0) {
-              const char* gB = T_buf + (int64_t)h0 * kRowBytesB;
-              if (!run_gemm<P>(sh, stage, ring_bytes, rg, ah, ap1 * kRowBytes, ap1, gB, nh * kRowBytesB,
-                               (int64_t)ntot * kRowBytesB, (2 * ap) / 16, mr, nh, pol_first, pol_last, stall, a.prof ? &s_prof : nullptr)) {
+            if (tid == 0 || tid == kProducer) {
+              const Gemm g{ah, (uint32_t)(ap1 * kRowBytes), ap1, T_buf + (int64_t)h0 * kRowBytesB,
+                           (uint32_t)(nh * kRowBytesB), (int64_t)ntot * kRowBytesB, (2 * ap) / 16, mr, nh};
+              const bool ok = tid == 0 ? gemm_consume<P>(sh, stage, consumed, waited, g, stall, pf)
+                                       : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf);
+              if (!ok) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
               }
@@ -682,7 +750,8 @@ finish:
     // writing its TMEM: wait (bounded) for every copy issued but not yet
     // waited for, then for every MMA this thread issued, before the TMEM is
     // freed and the CTA's shared memory is released.
-    for (uint32_t gi = rg.waited; gi < rg.issued; ++gi) wait_bar(&sh.full[gi % kSlots], (gi / kSlots) & 1);
+    const uint32_t issued = *(volatile uint32_t*)&sh.issued;
+    for (uint32_t gi = waited; gi < issued; ++gi) wait_bar(&sh.full[gi % kSlots], (gi / kSlots) & 1);
     commit(&sh.drain);
     wait_bar(&sh.drain, 0);
   }

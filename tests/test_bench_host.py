@@ -109,3 +109,29 @@ def test_roofline_traffic_only_for_the_captured_schedule(monkeypatch):
     assert bench.roofline_traffic("split", {**sch, "us_per_pair": 7.0}, 10) is not None
     monkeypatch.setattr(bench, "TC_DRAM_BYTES_PER_PAIR", None)
     assert bench.roofline_traffic("split", sch, 10) is None
+
+
+def test_issued_macs_follow_the_kernel_tiling():
+    """Brute-force replay of the kernel's tile loops (one ket per tile)."""
+    rng = np.random.default_rng(4)
+    N, n = 5, 7
+    dims = np.ones((N, n + 1), dtype=np.int64)
+    dims[:, 1:-1] = rng.integers(1, 129, size=(N, n - 1))
+    pad = lambda x: (int(x) + 15) // 16 * 16
+    ref = 0.0
+    for i in range(N):
+        for j in range(i + 1, N):
+            for k in range(n):
+                ap, ap1 = pad(dims[i, k]), pad(dims[i, k + 1])
+                bp, bp1 = pad(dims[j, k]), pad(dims[j, k + 1])
+                rows = 2 * bp1
+                M, nt = (64, 1) if rows <= 64 else (128, (rows + 127) // 128)
+                for _t in range(nt):
+                    for h0 in range(0, ap, 64):
+                        nh = min(64, ap - h0)
+                        ref += (bp // 16) * 3 * 2 * M * (2 * nh) * 16      # HS1 chunks x MMAs
+                M2 = 64 if ap1 <= 64 else 128
+                for h0 in range(0, bp1, 64):
+                    nh = min(64, bp1 - h0)
+                    ref += (2 * ap // 16) * 3 * 2 * M2 * (2 * nh) * 16       # HS2
+    assert bench.issued_macs(dims) == pytest.approx(ref, rel=1e-12)
