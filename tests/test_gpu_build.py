@@ -45,6 +45,12 @@ def test_tiny_exact_states_match_statevector(qk):
     K, _ = qk.qk_gram(A, prec="fp64")
     Kref = statevector.gram(w.X, w.d, w.reps, w.gamma)
     assert np.max(np.abs(K.cpu().numpy() - Kref)) < 1e-12
+    # the stored statevector Gram (tests/golden), FP64 and split paths
+    from test_golden import load_tiny_golden
+    Kg = load_tiny_golden()
+    assert np.max(np.abs(K.cpu().numpy() - Kg)) < 1e-12
+    Ks, _ = qk.qk_gram(A, prec="split")
+    assert np.max(np.abs(Ks.cpu().numpy() - Kg)) < 1e-5
 
 
 @pytest.mark.parametrize("n,d,reps,gamma,chi,eps,N", [

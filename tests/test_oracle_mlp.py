@@ -71,6 +71,15 @@ def test_pair_features_symmetric():
     assert np.allclose(f1[2, :4], 0)
 
 
+def test_pair_features_by_hand():
+    """x = (1, 2), y = (3, 5): squared differences (4, 9), midpoints (2, 3.5);
+    a pair of a point with itself gives (0, 0, x)."""
+    Xa = np.array([[1.0, 2.0]])
+    Xb = np.array([[3.0, 5.0], [1.0, 2.0]])
+    f = mlp.pair_features(Xa, Xb, np.array([[0, 0], [0, 1]]))
+    assert np.array_equal(f, np.array([[4.0, 9.0, 2.0, 3.5], [0.0, 0.0, 1.0, 2.0]]))
+
+
 def test_conformal_coverage():
     """For exchangeable residuals the split-conformal bound covers a fresh
     point with probability >= 1 - alpha."""
