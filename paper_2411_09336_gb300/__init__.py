@@ -65,6 +65,7 @@ _sig("qk_gram_pairs_noalloc", [_vp, _vp, _vp, _i64, _vp, _vp])
 _sig("qk_debug_stall_next_split", [_i32])
 _sig("qk_debug_tc_profile", [_i32])
 _sig("qk_debug_tc_max_ctas", [_i32])
+_sig("qk_debug_tc_variant", [_i32])
 _sig("qk_last_tc_profile", [_vp, C.POINTER(_i32)])
 _sig("qk_tune_split", [_vp, _vp, C.c_int, _vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_f64)])
 _sig("qk_set_split_schedule", [_vp, _vp, C.c_int, _i32, _i32])
@@ -315,6 +316,13 @@ def qk_debug_tc_profile(on: bool = True) -> None:
 def qk_debug_tc_max_ctas(ctas: int = 0) -> None:
     """Test knob: cap the tensor-core kernel's grid (0: default)."""
     _check(_lib.qk_debug_tc_max_ctas(int(ctas)), "qk_debug_tc_max_ctas")
+
+
+def qk_debug_tc_variant(flags: int) -> None:
+    """Operand-stream variant of the tensor-core kernel (bits: 1 GEMM-block L2
+    prefetch, 2 next-site L2 prefetch, 4 normal L2 priority for the static
+    operands; see include/qk.h)."""
+    _check(_lib.qk_debug_tc_variant(int(flags)), "qk_debug_tc_variant")
 
 
 def qk_last_tc_profile() -> dict:

@@ -26,7 +26,8 @@
 // thread (warp 1) issues the bulk copies into a byte ring of up to eight
 // chunks and reclaims the space of chunks whose MMAs have completed, while
 // thread 0 waits for each chunk and issues its MMAs, so copy issue and MMA
-// issue overlap; three CTAs per SM overlap one another's epilogues.  Every
+// issue overlap; four CTAs per SM (P = 2; three at P = 3) overlap one
+// another's epilogues and copy waits.  Every
 // wait is bounded in time and reports QK_ERR_TIMEOUT instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -67,14 +68,20 @@ constexpr int kNMax = QK_TC_NMAX;
 constexpr int kTmemCols = 2 * kNMax;
 static_assert(kNMax == 64 || kNMax == 128, "one MMA covers 64 or 128 complex columns");
 static_assert(kCtas * kTmemCols <= 512, "the CTAs of an SM share its 512 TMEM columns");
+#ifndef QK_TC_RING_MIN
+#define QK_TC_RING_MIN 1
+#endif
 template <int P>
 struct Stage {
   static constexpr int A = 128 * 32 * 2 * P;    // 128 rows of one 16-wide K chunk, all planes
   static constexpr int B = kNMax * 32 * 3 * P;  // up to kNMax complex rows, [re; im; -re] per part
   static constexpr int want = P == 2 ? kCtas : (kCtas < 3 ? kCtas : 3);
   static constexpr int fit = ((220 * 1024 / want) / 1024) * 1024;
-  // ring: what the SM's shared memory allows per CTA, at least two chunks
-  static constexpr int ring = fit > 2 * (A + B) ? fit : 2 * (A + B);
+  // ring: what the SM's shared memory allows per CTA, at least QK_TC_RING_MIN
+  // chunks of the largest size (one is enough for correctness: the producer
+  // restarts an empty ring at offset 0)
+  static constexpr int ring = fit > QK_TC_RING_MIN * (A + B) ? fit : QK_TC_RING_MIN * (A + B);
+  static_assert(QK_TC_RING_MIN >= 1, "the ring holds at least one chunk of the largest size");
   // CTAs that actually fit an SM with that ring (static shared memory and the
   // per-CTA reservation included), at most the requested count
   static constexpr int fits = (228 * 1024) / (ring + 2048);
@@ -210,6 +217,22 @@ __device__ inline void bulk_load(void* dst, const void* src, uint32_t bytes, uin
       : "memory");
 }
 
+// L2 prefetch of a byte range (16-byte aligned start, size a multiple of 16),
+// in pieces of at most 32 KB; nothing waits for it
+__device__ inline void prefetch_l2(const void* src, uint32_t bytes) {
+  const char* p = static_cast<const char*>(src);
+  for (uint32_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t b = bytes - o < 32768u ? bytes - o : 32768u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(b) : "memory");
+  }
+}
+
+__device__ inline uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ inline void st_v4_last(void* p, uint4 v, uint64_t policy) {
   asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
                "r"(v.w), "l"(policy)
@@ -221,16 +244,26 @@ __device__ inline void expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ inline void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive accumulator columns of this thread's lane from each of two
+// TMEM addresses (the re and im halves), one wait for both loads
+__device__ inline void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+  uint32_t r[16], q[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+        "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+      : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) {
+    va[i] = __uint_as_float(r[i]);
+    vb[i] = __uint_as_float(q[i]);
+  }
 }
 
 // split 16 floats into P bf16 planes, two values per cvt.rn.bf16x2
@@ -302,6 +335,7 @@ struct TcArgs {
   unsigned long long* queue;
   int* err;
   int stall;                 // test hook: CTA 0 lets one bounded wait run out mid-GEMM
+  int flags;                 // kPrefetchGemm | kPrefetchSite | kStaticNormal
   unsigned long long* prof;  // optional [kProfN] cycle counters summed over CTAs
 };
 
@@ -317,6 +351,15 @@ struct TcProf {  // in shared memory, written by thread 0 only
 };
 
 constexpr int kSlots = 8;  // chunks in flight at most (one mbarrier pair each)
+// Operand-stream variants (qk_debug_tc_variant): L2 prefetch of a GEMM's
+// whole static block when its first chunk is issued (the ring holds only
+// two or three chunks); L2 prefetch of the next site's static blocks (bra
+// and kets) when a site starts; static operands loaded with the normal L2
+// priority instead of evict-first.
+constexpr int kPrefetchGemm = 1, kPrefetchSite = 2, kStaticNormal = 4;
+#ifndef QK_TC_VARIANT
+#define QK_TC_VARIANT 0
+#endif
 constexpr int kProducer = 32;  // the thread (lane 0 of warp 1) that issues the bulk copies
 
 // test hook (qk_debug_stall_next_split): the next tensor-core launch lets one
@@ -327,6 +370,8 @@ std::atomic<int> g_stall_next{0};
 std::atomic<int> g_tc_profile{0};
 // test knob (qk_debug_tc_max_ctas): cap on the grid of the tensor-core kernel (0: none)
 std::atomic<int> g_tc_max_ctas{0};
+// operand-stream variant flags of the next launches (kPrefetchGemm, ...)
+std::atomic<int> g_tc_variant{QK_TC_VARIANT};
 thread_local unsigned long long g_tc_prof_last[kProfN] = {};
 thread_local int g_tc_prof_ctas = 0;
 thread_local unsigned long long* g_tc_prof_pending = nullptr;
@@ -413,16 +458,24 @@ __device__ inline bool wait_or_abort(TcShared& sh, uint64_t* bar, uint32_t parit
 // oldest live chunk always ends.
 template <int P>
 __device__ bool gemm_produce(TcShared& sh, char* ring, Ring& rg, const Gemm& g, uint64_t pol_a, uint64_t pol_b,
-                             TcProf* pf) {
+                             bool prefetch, TcProf* pf) {
   const unsigned long long t_in = pf ? clock64() : 0ull;
+  // the static chunks beyond the ring's depth then come from L2
+  if (prefetch && g.nchunks > 1) prefetch_l2(g.gA, (uint32_t)g.nchunks * g.a_bytes);
   constexpr uint32_t R = Stage<P>::ring;
   const uint32_t a_span = a_span_of<P>(g), size = a_span + g.b_bytes;
   const uint32_t g0 = rg.produced;
   for (int p = 0; p < g.nchunks; ++p) {
     const uint32_t gi = g0 + p;
-    const uint32_t pad = rg.wpos + size > R ? R - rg.wpos : 0;  // a chunk never straddles the end
-    const uint32_t need = pad + size;
-    while (rg.used + need > R || gi - rg.released >= (uint32_t)kSlots) {
+    uint32_t pad, need;
+    for (;;) {
+      if (rg.used == 0) rg.wpos = 0;  // an empty ring restarts at its start
+      pad = rg.wpos + size > R ? R - rg.wpos : 0;  // a chunk never straddles the end
+      need = pad + size;
+      // fits, or wait for the oldest live chunk (one exists whenever the
+      // ring is not empty or the slots are all taken; an empty ring always
+      // fits a chunk since R >= size)
+      if (rg.used + need <= R && gi - rg.released < (uint32_t)kSlots) break;
       const uint32_t j = rg.released, js = j % kSlots;
       const unsigned long long t0 = pf ? clock64() : 0ull;
       if (!wait_or_abort(sh, &sh.empty[js], (j / kSlots) & 1)) return false;
@@ -550,7 +603,9 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sh.tmem;
-  const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+  const uint64_t pol_first = (a.flags & kStaticNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t pol_last = policy_evict_last();
+  const bool pf_gemm = (a.flags & kPrefetchGemm) != 0;
   Ring rg;                       // operand ring (the producer thread's state)
   uint32_t consumed = 0, waited = 0;  // the MMA thread's chunk counts
   bool stall = a.stall && blockIdx.x == 0;  // test hook, first GEMM of >= 2 chunks
@@ -611,6 +666,15 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
     const int32_t* da = a.a_dims + (int64_t)i * (n + 1);
     for (int k = 0; k < n; ++k) {
       const int ap = pad16(da[k]), ap1 = pad16(da[k + 1]);
+      if ((a.flags & kPrefetchSite) && tid == kProducer && k + 1 < n) {
+        // the next site's bra block Ah (p1 x 2 p0) and ket blocks Bt (2 p1 x p0)
+        prefetch_l2(a.a_arena + a.a_ah[(int64_t)i * n + k + 1], (uint32_t)(ap1 * 2 * pad16(da[k + 2]) * 2 * kPlanes));
+        for (int q = 0; q < nk; ++q) {
+          const int32_t* db = a.b_dims + (int64_t)jj[q] * (n + 1);
+          prefetch_l2(a.b_arena + a.b_bt[(int64_t)jj[q] * n + k + 1],
+                      (uint32_t)(2 * pad16(db[k + 2]) * pad16(db[k + 1]) * 2 * kPlanes));
+        }
+      }
       int q0 = 0;
       while (q0 < nk) {
         // group kets while their stacked columns fit one MMA (<= kNMax); a
@@ -641,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                              et + (int64_t)h0 * kRowBytesB, (uint32_t)(nh * kRowBytesB),
                              (int64_t)ap * kRowBytesB, bp / 16, mr, nh};
                 const bool ok = tid == 0 ? gemm_consume<P>(sh, stage, consumed, waited, g, stall, pf)
-                                         : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf);
+                                         : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf_gemm, pf);
                 if (!ok) {
                   sh.abort = 1;
                   atomicExch(a.err, 1);
@@ -664,8 +728,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                 __nv_bfloat16* Tb = reinterpret_cast<__nv_bfloat16*>(T_buf);
                 for (int c = 0; c < nh; c += 16) {
                   float re[16], im[16];
-                  tmem_ld16(tmem + lane_base + c, re);
-                  tmem_ld16(tmem + lane_base + nh + c, im);
+                  tmem_ld16x2(tmem + lane_base + c, tmem + lane_base + nh + c, re, im);
                   if (r >= 0 && R < rows) {
                     const int s = R / bp1, b1 = R % bp1;
                     store_row16<P>(Tb, nb[q] + b1, s * ap + h0 + c, ntot, re, im, pol_last);
@@ -689,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
               const Gemm g{ah, (uint32_t)(ap1 * kRowBytes), ap1, T_buf + (int64_t)h0 * kRowBytesB,
                            (uint32_t)(nh * kRowBytesB), (int64_t)ntot * kRowBytesB, (2 * ap) / 16, mr, nh};
               const bool ok = tid == 0 ? gemm_consume<P>(sh, stage, consumed, waited, g, stall, pf)
-                                       : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf);
+                                       : gemm_produce<P>(sh, stage, rg, g, pol_first, pol_last, pf_gemm, pf);
               if (!ok) {
                 sh.abort = 1;
                 atomicExch(a.err, 1);
@@ -716,15 +779,13 @@ __global__ void __launch_bounds__(kThreads, Stage<P>::ctas_per_sm) tc_overlap_ke
                 __nv_bfloat16* et = reinterpret_cast<__nv_bfloat16*>(scr + q * a.et_stride);
                 for (int c = c0; c < c1; c += 16) {
                   float re[16], im[16];
-                  tmem_ld16(tmem + lane_base + c, re);
-                  tmem_ld16(tmem + lane_base + nh + c, im);
+                  tmem_ld16x2(tmem + lane_base + c, tmem + lane_base + nh + c, re, im);
                   if (r >= 0 && r < ap1) store_row16<P>(et, r, h0 + c - nb[q], ap1, re, im, pol_last);
                 }
               } else if (nb[q] >= h0) {
                 // last site: 1 x 1 environments, z = E[0][0]
                 float re[16], im[16];
-                tmem_ld16(tmem + lane_base + c0, re);
-                tmem_ld16(tmem + lane_base + nh + c0, im);
+                tmem_ld16x2(tmem + lane_base + c0, tmem + lane_base + nh + c0, re, im);
                 if (r == 0) {
                   const double zr = re[0], zi = im[0];
                   const double kv = zr * zr + zi * zi;
@@ -990,6 +1051,7 @@ qk_status launch_tc(const qk_mps_batch* A, const qk_mps_batch* B, int mode, cons
   a.queue = queue;
   a.err = err;
   a.stall = g_stall_next.exchange(0);
+  a.flags = g_tc_variant.load();
   a.prof = nullptr;
   if (g_tc_profile.load() && !g_tc_prof_pending) {
     QK_CUDA(cudaMallocAsync(&a.prof, sizeof(unsigned long long) * kProfN, st));
@@ -1307,6 +1369,12 @@ extern "C" qk_status qk_last_tc_profile(double* counters, int32_t* ctas) {
   if (counters)
     for (int f = 0; f < qk::kProfN; ++f) counters[f] = (double)qk::g_tc_prof_last[f];
   if (ctas) *ctas = qk::g_tc_prof_ctas;
+  return QK_OK;
+}
+
+extern "C" qk_status qk_debug_tc_variant(int32_t flags) {
+  if (flags < 0 || flags > 7) return qk::fail(QK_ERR_INVALID_ARG, "qk_debug_tc_variant: flags must be in [0, 7]");
+  qk::g_tc_variant.store(flags);
   return QK_OK;
 }
 
