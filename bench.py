@@ -47,10 +47,11 @@ BENCH_SCHEDULE = {"kets_per_tile": 1, "band": 128}
 # the n=165, d=6, chi_max=128 circuit with BENCH_SCHEDULE, from one ncu
 # capture of a smaller symmetric Gram of the same circuit (the capture's
 # dram__bytes_read.sum + dram__bytes_write.sum divided by its pairs; see
-# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 256.10 GB for the
+# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 350.31 GB for the
 # 11,476 pairs of a 152-state Gram).  Per-pair time is the same at 152 and
-# 1216 states, so the per-pair traffic is taken as independent of N.
-TC_DRAM_BYTES_PER_PAIR = 256.102518784e9 / 11476
+# 1216 states (6.78 and 6.66 us), so the per-pair traffic is taken as
+# independent of N.
+TC_DRAM_BYTES_PER_PAIR = 350.30999936e9 / 11476
 
 
 def roofline_traffic(prec, schedule, pairs):
