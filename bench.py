@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the subset, load-only, inference and surrogate legs")
+    p.add_argument("--depth-sweep", action="store_true",
+                   help="add the Table III depth sweep (50 features, d=1, gamma=1, r=2..20)")
     p.add_argument("--surrogate-epochs", type=int, default=20)
     p.add_argument("--surrogate-test", type=int, default=304, help="test states of the surrogate block")
     return p.parse_args()
@@ -416,6 +418,64 @@ def svm_leg(w, K_train, K_test, rank, N, test_rows):
     return out
 
 
+DEPTHS = (2, 4, 8, 12, 16, 20)
+
+
+def depth_sweep_leg(qk, w, rank, n_train=800, n_test=200, depths=DEPTHS):
+    """The depth regime of Table III: 50 features, d = 1, gamma = 1, the
+    ansatz repeated r times.  Per r: the states' bond dimensions, the
+    concentration of the off-diagonal kernel, build and Gram times, and the
+    best test AUC of the quantum-kernel SVM (C from 0.01 to 4), next to the
+    Gaussian kernel of Eq. 9 on the same 50 features.  Data: the first 50
+    columns of this rank's c165 training and test rows, min-max scaled into
+    [0, 2] over the training rows (the paper's data preparation, Sec. II-A;
+    test rows clipped to that interval)."""
+    import torch
+    from paper_2411_09336_gb300 import classify
+    tr0, te0 = rank * n_train, rank * n_test
+    Xtr = w.X_train[tr0:tr0 + n_train, :50]
+    Xte = w.X_test[te0:te0 + n_test, :50]
+    lo, hi = Xtr.min(axis=0), Xtr.max(axis=0)
+    span = np.where(hi > lo, hi - lo, 1.0)
+    Xtr = np.ascontiguousarray(2.0 * (Xtr - lo) / span)
+    Xte = np.ascontiguousarray(np.clip(2.0 * (Xte - lo) / span, 0.0, 2.0))
+    ytr = w.y[tr0:tr0 + n_train]
+    yte = w.y[w.n_train + te0:w.n_train + te0 + n_test]
+    Cs = [0.01, 0.1, 0.5, 1.0, 2.0, 4.0]
+
+    def best_auc(Ktr, Kte):
+        return max(classify.roc_auc(yte, classify.SVM(C=C).fit(Ktr, ytr).decision_function(Kte)) for C in Cs)
+
+    alpha = classify.gaussian_alpha(Xtr)
+    out = {"features": 50, "d": 1, "gamma": 1.0, "chi_max": 128, "eps": 1e-8, "train": n_train, "test": n_test,
+           "gaussian_best_auc": round(best_auc(classify.gaussian_kernel(Xtr, Xtr, alpha),
+                                               classify.gaussian_kernel(Xte, Xtr, alpha)), 4),
+           "by_depth": []}
+    for r in depths:
+        torch.cuda.synchronize()
+        t0 = time.time()
+        A = qk.qk_build_states(Xtr, 1, r, 1.0, 128, 1e-8, store="c64")
+        T = qk.qk_build_states(Xte, 1, r, 1.0, 128, 1e-8, store="c64")
+        torch.cuda.synchronize()
+        t1 = time.time()
+        Ktr, _ = qk.qk_gram(A, prec="split")
+        Kte, _ = qk.qk_gram(T, A, prec="split")
+        torch.cuda.synchronize()
+        t2 = time.time()
+        Ktr, Kte = Ktr.cpu().numpy(), Kte.cpu().numpy()
+        off = Ktr[np.triu_indices(n_train, 1)]
+        dims = A.bond_dims()
+        out["by_depth"].append({
+            "r": r, "mean_chi": round(float(dims[:, 1:-1].mean()), 2), "max_chi": int(dims.max()),
+            "build_s": round(t1 - t0, 2), "gram_s": round(t2 - t1, 3),
+            "median_K": float(np.median(off)), "mean_K": float(off.mean()),
+            "frac_K_below_1e-4": round(float(np.mean(off < 1e-4)), 4),
+            "quantum_best_auc": round(best_auc(Ktr, Kte), 4)})
+        A.free()
+        T.free()
+    return out
+
+
 # --------------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -562,6 +622,9 @@ def run_ours(a):
         extra["inference_one_point"] = {"build_s": round(t1 - t0, 3), "row_s": round(t2 - t1, 4),
                                         "total_s": round(t2 - t0, 3), "train_states": N}
         T1.free()
+        # ---- depth sweep (Table III regime; about 5 minutes, so on request)
+        if a.depth_sweep:
+            extra["depth_sweep"] = depth_sweep_leg(qk, w, rank)
 
     # kernels of one split qk_gram on a symmetric batch: the tensor-core sweep,
     # the self-overlaps, the refinement selection, and, when entries were

@@ -281,13 +281,16 @@ qk_status qk_debug_tc_profile(int32_t on);
  * depend on it; only the schedule's spread over the SMs changes. */
 qk_status qk_debug_tc_max_ctas(int32_t ctas);
 /* Operand-stream variant of the next tensor-core overlap launches (the
- * paper has no counterpart): a bit set in `flags` (0..7) turns on
+ * paper has no counterpart): a bit set in `flags` (0..15) turns on
  *   1  an L2 prefetch of a GEMM's whole static operand block when its first
  *      chunk is issued,
  *   2  an L2 prefetch of the next site's static blocks when a site starts,
- *   4  the normal L2 priority for the static operands (default: evict-first).
+ *   4  the normal L2 priority for the static operands (default: evict-first),
+ *   8  dropping the L2 lines of a consumed environment or half-step block
+ *      without write-back (the next reader finds it rewritten in full).
  * Results do not depend on it (the same MMAs on the same data); only where
- * the operand bytes come from changes.  QK_ERR_INVALID_ARG outside 0..7. */
+ * the operand bytes come from changes.  The default is 8 (the fastest
+ * measured).  QK_ERR_INVALID_ARG outside 0..15. */
 qk_status qk_debug_tc_variant(int32_t flags);
 qk_status qk_last_tc_profile(double* counters, int32_t* ctas);
 

@@ -321,7 +321,8 @@ def qk_debug_tc_max_ctas(ctas: int = 0) -> None:
 def qk_debug_tc_variant(flags: int) -> None:
     """Operand-stream variant of the tensor-core kernel (bits: 1 GEMM-block L2
     prefetch, 2 next-site L2 prefetch, 4 normal L2 priority for the static
-    operands; see include/qk.h)."""
+    operands, 8 drop consumed scratch lines without write-back; see
+    include/qk.h)."""
     _check(_lib.qk_debug_tc_variant(int(flags)), "qk_debug_tc_variant")
 
 

@@ -187,6 +187,34 @@ def test_split_schedules_agree_and_tuner(qk):
         qk.qk_tune_split(A, prec="fp64")
 
 
+def test_operand_stream_variants_give_identical_entries(qk):
+    """The operand-stream variants (L2 prefetch, cache priority, dropping
+    consumed scratch lines) move the same bytes into the same MMAs: the
+    entries repeat bit for bit, symmetric and rectangular, multi-ket tiles
+    included, and match the oracle."""
+    states = ragged_states(30, 14, seed=41, chis=(20, 33, 48, 70))
+    A = qk.qk_mps_import(states, store="c64")
+    B = qk.qk_mps_import(states[:11], store="c64")
+    ref = overlap.gram([mps.round_sites(s, "c64") for s in states])
+    try:
+        for kets in (1, 3):
+            qk.qk_set_split_schedule(A, prec="split", kets_per_tile=kets, band=16)
+            qk.qk_set_split_schedule(A, B, prec="split", kets_per_tile=kets, band=16)
+            base = None
+            for flags in (0, 1, 2, 4, 8, 15):
+                qk.qk_debug_tc_variant(flags)
+                K = qk.qk_gram(A, prec="split")[0].cpu().numpy()
+                R = qk.qk_gram(A, B, prec="split")[0].cpu().numpy()
+                if base is None:
+                    base = (K, R)
+                    check(K, ref)
+                assert np.array_equal(K, base[0]) and np.array_equal(R, base[1]), (kets, flags)
+        with pytest.raises(qk.QKError):
+            qk.qk_debug_tc_variant(16)
+    finally:
+        qk.qk_debug_tc_variant(8)
+
+
 def test_bounded_wait_runs_out_and_device_stays_usable(qk):
     """A bounded mbarrier wait that runs out (test hook: a wait on a barrier
     nothing arrives at, with copies and MMAs in flight) makes the call fail
