@@ -44,14 +44,15 @@ METRIC = "Gram entries/s (n=165, chi=128), split-precision vs FP64 path on 1 GB3
 BENCH_SCHEDULE = {"kets_per_tile": 1, "band": 128}
 
 # DRAM bytes (read + write) per off-diagonal pair of tc_overlap_kernel<2> at
-# the n=165, d=6, chi_max=128 circuit with BENCH_SCHEDULE, from one ncu
-# capture of a smaller symmetric Gram of the same circuit (the capture's
-# dram__bytes_read.sum + dram__bytes_write.sum divided by its pairs; see
-# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 350.31 GB for the
+# the n=165, d=6, chi_max=128 circuit with BENCH_SCHEDULE and the default
+# operand-stream variant, from one ncu capture of a smaller symmetric Gram
+# of the same circuit (the capture's dram__bytes_read.sum +
+# dram__bytes_write.sum divided by its pairs; see
+# profiles/tc_overlap_kernel_c165_152states_k1b128.md: 232.62 GB for the
 # 11,476 pairs of a 152-state Gram).  Per-pair time is the same at 152 and
-# 1216 states (6.78 and 6.66 us), so the per-pair traffic is taken as
+# 1216 states (6.79 and 6.68 us), so the per-pair traffic is taken as
 # independent of N.
-TC_DRAM_BYTES_PER_PAIR = 350.30999936e9 / 11476
+TC_DRAM_BYTES_PER_PAIR = 232.617735936e9 / 11476
 
 
 def roofline_traffic(prec, schedule, pairs):
