@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "qk_internal.h"
@@ -149,10 +150,66 @@ __global__ void __launch_bounds__(kThreads) diag_kernel(DiagArgs a) {
 
 }  // namespace
 
-// K[i*ldk + i] for every state of a complex64 batch; states that are not
-// left-canonical are re-done by the FP64 sweep.  Returns the FP64 count.
-qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st,
-                             int64_t* n_fp64) {
+// A second, non-blocking stream per device for the self-overlaps, so that
+// they run beside the FP64 re-evaluation of a split Gram (both are a few
+// long-running CTAs); created on first use.
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    streams[dev] = nullptr;
+    cudaGetLastError();
+  }
+  return streams[dev];
+}
+
+// Launches diag_kernel for every state of a complex64 batch on `st` (no
+// synchronisation); diag_finish reads the flags once `st` is done.
+qk_status diag_launch(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st, DiagPending* d) {
+  d->st = st;
+  d->flag = nullptr;
+  d->N = A->N;
+  if (A->N == 0 || A->store != QK_STORE_C64) return QK_OK;
+  int dev = 0, sms = 0;
+  QK_CUDA(cudaGetDevice(&dev));
+  QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t N = A->N;
+  const int64_t cap = (int64_t)A->chi_cap * A->chi_cap;
+  const int64_t ctas = std::min<int64_t>((int64_t)4 * sms, N);
+  float2* scratch = nullptr;
+  int* queue = nullptr;
+  QK_CUDA(cudaMallocAsync(&scratch, sizeof(float2) * 4 * cap * ctas, st));
+  QK_CUDA(cudaMallocAsync(&queue, sizeof(int), st));
+  QK_CUDA(cudaMallocAsync(&d->flag, sizeof(int32_t) * N, st));
+  QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), st));
+  DiagArgs a;
+  a.site_ptr = A->d_site_ptr;
+  a.dims = A->d_dims;
+  a.n = A->n;
+  a.N = N;
+  a.K = dK;
+  a.ldk = ldk;
+  a.flag = d->flag;
+  a.scratch = scratch;
+  a.cap = cap;
+  a.queue = queue;
+  timer_mark(false, st);
+  diag_kernel<<<(int)ctas, kThreads, 0, st>>>(a);
+  timer_mark(true, st);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(scratch, st);
+  cudaFreeAsync(queue, st);
+  if (e != cudaSuccess) return cuda_fail(e, "diag_kernel");
+  return QK_OK;
+}
+
+// Waits for the launch, then re-does by the FP64 sweep (on st_fp64) every
+// state that is not left-canonical, or every state of a complex128 batch.
+qk_status diag_finish(const qk_mps_batch* A, double* dK, int64_t ldk, DiagPending* d, cudaStream_t st_fp64,
+                      int64_t* n_fp64) {
   if (n_fp64) *n_fp64 = 0;
   const int64_t N = A->N;
   if (N == 0) return QK_OK;
@@ -160,39 +217,11 @@ qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cud
   if (A->store != QK_STORE_C64) {
     for (int64_t i = 0; i < N; ++i) fallback.push_back((int32_t)i);
   } else {
-    int dev = 0, sms = 0;
-    QK_CUDA(cudaGetDevice(&dev));
-    QK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t cap = (int64_t)A->chi_cap * A->chi_cap;
-    const int64_t ctas = std::min<int64_t>((int64_t)4 * sms, N);
-    float2* scratch = nullptr;
-    int* queue = nullptr;
-    int32_t* flag = nullptr;
-    QK_CUDA(cudaMallocAsync(&scratch, sizeof(float2) * 4 * cap * ctas, st));
-    QK_CUDA(cudaMallocAsync(&queue, sizeof(int), st));
-    QK_CUDA(cudaMallocAsync(&flag, sizeof(int32_t) * N, st));
-    QK_CUDA(cudaMemsetAsync(queue, 0, sizeof(int), st));
-    DiagArgs a;
-    a.site_ptr = A->d_site_ptr;
-    a.dims = A->d_dims;
-    a.n = A->n;
-    a.N = N;
-    a.K = dK;
-    a.ldk = ldk;
-    a.flag = flag;
-    a.scratch = scratch;
-    a.cap = cap;
-    a.queue = queue;
-    timer_mark(false, st);
-    diag_kernel<<<(int)ctas, kThreads, 0, st>>>(a);
-    timer_mark(true, st);
-    cudaError_t e = cudaGetLastError();
     std::vector<int32_t> hf(N);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), flag, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFreeAsync(scratch, st);
-    cudaFreeAsync(queue, st);
-    cudaFreeAsync(flag, st);
+    cudaError_t e = cudaMemcpyAsync(hf.data(), d->flag, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, d->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->st);
+    cudaFreeAsync(d->flag, d->st);
+    d->flag = nullptr;
     if (e != cudaSuccess) return cuda_fail(e, "diag_kernel");
     for (int64_t i = 0; i < N; ++i)
       if (hf[i]) fallback.push_back((int32_t)i);
@@ -201,14 +230,24 @@ qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cud
     std::vector<int32_t> hp(2 * fallback.size());
     for (size_t i = 0; i < fallback.size(); ++i) hp[2 * i] = hp[2 * i + 1] = fallback[i];
     int32_t* dp = nullptr;
-    QK_CUDA(cudaMallocAsync(&dp, sizeof(int32_t) * hp.size(), st));
-    QK_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(int32_t) * hp.size(), cudaMemcpyHostToDevice, st));
-    qk_status rc = overlap_fp64(A, A, dp, (int64_t)fallback.size(), dK, ldk, false, st);
-    cudaFreeAsync(dp, st);
+    QK_CUDA(cudaMallocAsync(&dp, sizeof(int32_t) * hp.size(), st_fp64));
+    QK_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(int32_t) * hp.size(), cudaMemcpyHostToDevice, st_fp64));
+    qk_status rc = overlap_fp64(A, A, dp, (int64_t)fallback.size(), dK, ldk, false, st_fp64);
+    cudaFreeAsync(dp, st_fp64);
     if (rc != QK_OK) return rc;
     if (n_fp64) *n_fp64 = (int64_t)fallback.size();
   }
   return QK_OK;
+}
+
+// K[i*ldk + i] for every state of a complex64 batch; states that are not
+// left-canonical are re-done by the FP64 sweep.  Returns the FP64 count.
+qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st,
+                             int64_t* n_fp64) {
+  DiagPending d;
+  qk_status rc = diag_launch(A, dK, ldk, st, &d);
+  if (rc != QK_OK) return rc;
+  return diag_finish(A, dK, ldk, &d, st, n_fp64);
 }
 
 }  // namespace qk

@@ -1291,50 +1291,64 @@ qk_status set_split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batc
 qk_status gram_split(int parts, const qk_mps_batch* A, const qk_mps_batch* B, double* dK, int64_t ldk,
                      double refine_floor, cudaStream_t st, int64_t* n_refined) {
   const bool sym = (A == B);
-  int64_t n_diag = 0;
   int* tc_err = nullptr;
   TcSchedule sch;
   qk_status rc = schedule_for(parts, A, B, sym ? 0 : 1, st, false, &sch, nullptr);
   if (rc != QK_OK) return rc;
   rc = launch_tc_parts(parts, A, B, sym ? 0 : 1, nullptr, 0, dK, ldk, st, &tc_err, sch);
-  if (rc == QK_OK && sym) {
-    // The diagonal (K_ii ~ 1, above the refinement ceiling by construction)
-    // comes from the isometry-defect recursion, which needs no FP64 sweep for
-    // left-canonical states; it runs after the strict upper triangle.
-    n_diag = A->N;
-    timer_set_phase(1);
-    rc = diag_self_overlaps(A, dK, ldk, st, nullptr);
-    timer_set_phase(0);
-  }
-  qk_status rc2 = tc_finish(tc_err, st);
-  if (rc == QK_OK) rc = rc2;
-  if (rc != QK_OK) return rc;
-  // FP64 re-evaluation of the off-diagonal entries below the floor and above
-  // the ceiling
+  // The off-diagonal entries below the floor and above the ceiling go to
+  // FP64; they are selected right behind the split kernel.
   const unsigned long long cap = sym ? (unsigned long long)A->N * (A->N + 1) / 2
                                      : (unsigned long long)A->N * B->N;
   int32_t* pairs = nullptr;
   unsigned long long* cnt = nullptr;
-  QK_CUDA(cudaMallocAsync(&pairs, sizeof(int32_t) * 2 * cap, st));
-  QK_CUDA(cudaMallocAsync(&cnt, sizeof(unsigned long long), st));
-  QK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-  select_refine_kernel<<<1024, 256, 0, st>>>(dK, ldk, (int)A->N, (int)B->N, sym ? 1 : 0, refine_floor,
-                                             QK_SPLIT_REFINE_ABOVE, pairs, cnt, cap);
   unsigned long long hc = 0;
-  QK_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-  QK_CUDA(cudaStreamSynchronize(st));
-  if (n_refined) *n_refined = (int64_t)hc + n_diag;
-  if (hc > 0) {
-    double* vals = nullptr;
-    QK_CUDA(cudaMallocAsync(&vals, sizeof(double) * hc, st));
-    timer_set_phase(1);
-    rc = overlap_fp64(A, B, pairs, (int64_t)hc, vals, 0, false, st);
-    timer_set_phase(0);
-    if (rc == QK_OK) scatter_kernel<<<1024, 256, 0, st>>>(pairs, vals, (int64_t)hc, dK, ldk, sym ? 1 : 0);
-    cudaFreeAsync(vals, st);
+  cudaError_t e = cudaSuccess;
+  if (rc == QK_OK) {
+    e = cudaMallocAsync(&pairs, sizeof(int32_t) * 2 * cap, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cnt, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+      select_refine_kernel<<<1024, 256, 0, st>>>(dK, ldk, (int)A->N, (int)B->N, sym ? 1 : 0, refine_floor,
+                                                 QK_SPLIT_REFINE_ABOVE, pairs, cnt, cap);
+      e = cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
+    }
   }
-  cudaFreeAsync(pairs, st);
-  cudaFreeAsync(cnt, st);
+  // synchronises st: the split kernel and the selection are done
+  qk_status rc2 = tc_finish(tc_err, st);
+  if (rc == QK_OK) rc = rc2;
+  if (rc == QK_OK && e != cudaSuccess) rc = cuda_fail(e, "gram_split: refinement selection");
+  if (rc == QK_OK && hc > 0) {
+    double* vals = nullptr;
+    e = cudaMallocAsync(&vals, sizeof(double) * hc, st);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaMallocAsync");
+    } else {
+      timer_set_phase(1);
+      rc = overlap_fp64(A, B, pairs, (int64_t)hc, vals, 0, false, st);
+      timer_set_phase(0);
+      if (rc == QK_OK) scatter_kernel<<<1024, 256, 0, st>>>(pairs, vals, (int64_t)hc, dK, ldk, sym ? 1 : 0);
+      cudaFreeAsync(vals, st);
+    }
+  }
+  int64_t n_diag = 0;
+  if (rc == QK_OK && sym) {
+    // The diagonal (K_ii ~ 1, above the refinement ceiling by construction)
+    // comes from the isometry-defect recursion, which needs no FP64 sweep for
+    // left-canonical states.  It runs on a side stream beside the FP64
+    // re-evaluation just launched (the two write disjoint entries; both are
+    // a few long CTAs), and the flagged states then take the FP64 sweep on st.
+    cudaStream_t side = side_stream();
+    DiagPending dp;
+    n_diag = A->N;
+    timer_set_phase(1);
+    rc = diag_launch(A, dK, ldk, side ? side : st, &dp);
+    if (rc == QK_OK) rc = diag_finish(A, dK, ldk, &dp, st, nullptr);
+    timer_set_phase(0);
+  }
+  if (n_refined) *n_refined = (int64_t)hc + n_diag;
+  if (pairs) cudaFreeAsync(pairs, st);
+  if (cnt) cudaFreeAsync(cnt, st);
   return rc;
 }
 

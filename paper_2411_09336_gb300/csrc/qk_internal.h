@@ -90,4 +90,16 @@ qk_status set_split_schedule(int parts, const qk_mps_batch* A, const qk_mps_batc
                              int32_t band);
 qk_status diag_self_overlaps(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st,
                              int64_t* n_fp64);
+// The same in two parts: the launch on `st`, and the wait for it with the
+// FP64 re-evaluation of the flagged states on `st_fp64`.
+struct DiagPending {
+  cudaStream_t st = nullptr;
+  int32_t* flag = nullptr;
+  int64_t N = 0;
+};
+qk_status diag_launch(const qk_mps_batch* A, double* dK, int64_t ldk, cudaStream_t st, DiagPending* d);
+qk_status diag_finish(const qk_mps_batch* A, double* dK, int64_t ldk, DiagPending* d, cudaStream_t st_fp64,
+                      int64_t* n_fp64);
+// a non-blocking stream of the current device for work beside the call's stream
+cudaStream_t side_stream();
 }  // namespace qk
