@@ -327,7 +327,11 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "entries/s", "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "c165: n=165 d=6 r=2 gamma=0.15 chi_max=128 eps=1e-8", "sample": sample},
+           "config": {"workload": f"c165: n=165 d=6 r=2 gamma=0.15 chi_max=128 eps=1e-8, {a.n_states} distinct "
+                                  f"built states per rank (complex64)",
+                      "states_per_rank": a.n_states,
+                      "gram": "symmetric, i<=j contracted, FP64 throughout (the oracle)",
+                      "sample": sample},
            "cpu_baseline": {"value": v, "unit": "entries/s", "cores": op.procs, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
