@@ -426,6 +426,25 @@ def svm_leg(w, K_train, K_test, rank, N, test_rows):
 DEPTHS = (2, 4, 8, 12, 16, 20)
 
 
+def table3_data(w, rank, n_train, n_test, features=50):
+    """This rank's rows for the depth sweep: the first `features` columns of
+    its c165 training and test rows, min-max scaled into [0, 2] over the
+    training rows (a constant column maps to 0), test rows clipped to
+    [0, 2]; labels alongside."""
+    tr0, te0 = rank * n_train, rank * n_test
+    Xtr = w.X_train[tr0:tr0 + n_train, :features]
+    Xte = w.X_test[te0:te0 + n_test, :features]
+    if len(Xtr) != n_train or len(Xte) != n_test:
+        raise ValueError("not enough rows for this rank")
+    lo, hi = Xtr.min(axis=0), Xtr.max(axis=0)
+    span = np.where(hi > lo, hi - lo, 1.0)
+    Xtr_s = np.ascontiguousarray(2.0 * (Xtr - lo) / span)
+    Xte_s = np.ascontiguousarray(np.clip(2.0 * (Xte - lo) / span, 0.0, 2.0))
+    ytr = w.y[tr0:tr0 + n_train]
+    yte = w.y[w.n_train + te0:w.n_train + te0 + n_test]
+    return Xtr_s, ytr, Xte_s, yte
+
+
 def depth_sweep_leg(qk, w, rank, n_train=800, n_test=200, depths=DEPTHS):
     """The depth regime of Table III: 50 features, d = 1, gamma = 1, the
     ansatz repeated r times.  Per r: the states' bond dimensions, the
@@ -437,15 +456,7 @@ def depth_sweep_leg(qk, w, rank, n_train=800, n_test=200, depths=DEPTHS):
     test rows clipped to that interval)."""
     import torch
     from paper_2411_09336_gb300 import classify
-    tr0, te0 = rank * n_train, rank * n_test
-    Xtr = w.X_train[tr0:tr0 + n_train, :50]
-    Xte = w.X_test[te0:te0 + n_test, :50]
-    lo, hi = Xtr.min(axis=0), Xtr.max(axis=0)
-    span = np.where(hi > lo, hi - lo, 1.0)
-    Xtr = np.ascontiguousarray(2.0 * (Xtr - lo) / span)
-    Xte = np.ascontiguousarray(np.clip(2.0 * (Xte - lo) / span, 0.0, 2.0))
-    ytr = w.y[tr0:tr0 + n_train]
-    yte = w.y[w.n_train + te0:w.n_train + te0 + n_test]
+    Xtr, ytr, Xte, yte = table3_data(w, rank, n_train, n_test)
     Cs = [0.01, 0.1, 0.5, 1.0, 2.0, 4.0]
 
     def best_auc(Ktr, Kte):

@@ -135,3 +135,18 @@ def test_issued_macs_follow_the_kernel_tiling():
                     nh = min(64, bp1 - h0)
                     ref += (2 * ap // 16) * 3 * 2 * M2 * (2 * nh) * 16       # HS2
     assert bench.issued_macs(dims) == pytest.approx(ref, rel=1e-12)
+
+
+def test_table3_data_scaled_into_0_2():
+    import workloads
+    w = workloads.c165()
+    Xtr, ytr, Xte, yte = bench.table3_data(w, 1, 800, 200)
+    assert Xtr.shape == (800, 50) and Xte.shape == (200, 50)
+    assert np.allclose(Xtr.min(axis=0), 0.0) and np.allclose(Xtr.max(axis=0), 2.0)
+    assert Xte.min() >= 0.0 and Xte.max() <= 2.0
+    # rank 1 takes training rows 800..1599 and test rows 200..399
+    raw = w.X_train[800:1600, :50]
+    assert np.allclose(Xtr[:, 3], 2 * (raw[:, 3] - raw[:, 3].min()) / np.ptp(raw[:, 3]))
+    assert np.array_equal(ytr, w.y[800:1600]) and np.array_equal(yte, w.y[6400 + 200:6400 + 400])
+    with pytest.raises(ValueError):
+        bench.table3_data(w, 8, 800, 200)
